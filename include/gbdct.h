@@ -1,0 +1,124 @@
+/*
+ * gbdct.h - C ABI of the GB300 (sm_103a) multi-dimensional DCT library.
+ *
+ * The library computes the 2D DCT-II and its exact inverse by the three-stage
+ * method of arXiv 2110.01172 (Section II-D, Algorithm 2; Section III): an
+ * even/odd reorder of the real input (Eq. 2d_dct_pre), a 2D real-to-complex
+ * FFT, and a twiddle-and-combine step that reads each conjugate-symmetric pair
+ * once (Section III-B, Eqs. four-elements and s-t).  The inverse runs the
+ * mirror image: the four-reads/two-writes twiddle preprocess (Eq. 2d_idct_pre),
+ * a complex-to-real 2D FFT and the inverse reorder (Eq. 2d_idct_post).  The
+ * reorder and the twiddle stages are fused into the first and last FFT passes,
+ * so a transform is two kernel launches and one on-chip/L2-resident
+ * intermediate.
+ *
+ * Conventions (all arrays are dense, row-major, last axis contiguous):
+ *   forward  X[k1,k2] = sum_{n1,n2} x[n1,n2] cos(pi k1 (2n1+1)/(2N1))
+ *                                          cos(pi k2 (2n2+1)/(2N2))
+ *            (unnormalised, Section II-A Eq. 2d-dct-definition);
+ *   inverse  the exact inverse of the forward map, i.e. the paper's IDCT
+ *            (DCT-III, Eq. 1b) applied per axis and scaled by 2/N per axis,
+ *            so inverse(forward(x)) == x.
+ *
+ * Every function returns a gbdct_status; no C++ exception crosses the ABI.
+ * Pointers named "device" must point to memory of the plan's CUDA device.
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * A plan may be used by one stream at a time (it owns one workspace).
+ */
+#ifndef GBDCT_H_
+#define GBDCT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbdct_plan_s* gbdct_plan_t;
+
+typedef enum gbdct_status {
+  GBDCT_OK = 0,
+  GBDCT_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, bad rank, dims <= 0 */
+  GBDCT_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+  GBDCT_ERR_OOM = 3,          /* device allocation failed at plan creation */
+  GBDCT_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+  GBDCT_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up */
+} gbdct_status;
+
+typedef enum gbdct_kind {
+  /* forward: 2D DCT-II; inverse: its exact inverse (scaled DCT-III). */
+  GBDCT_DCT2 = 0,
+  /* forward: 2D DST-II X = sum x sin(pi(2n1+1)(k1+1)/2N1) sin(..N2); inverse:
+     its exact inverse.  DST-II is not in the paper; it is computed through
+     DST-II(x)_k = DCT-II((-1)^n x)_{N-1-k} on each axis. */
+  GBDCT_DST2 = 1,
+  /* inverse: IDCT on axis 0 and IDXST on axis 1 (Section V-B, Eq. idxst,
+     "IDCT_IDXST"); forward: the exact inverse of that map. */
+  GBDCT_IDCT_IDXST = 2,
+  /* inverse: IDXST on axis 0 and IDCT on axis 1 ("IDXST_IDCT"); forward: its
+     exact inverse. */
+  GBDCT_IDXST_IDCT = 3
+} gbdct_kind;
+
+typedef enum gbdct_dtype {
+  GBDCT_F32 = 0               /* float32 input and output, float32 arithmetic */
+} gbdct_dtype;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* gbdct_status_string(gbdct_status status);
+
+/* Library version string, e.g. "gbdct 0.1.0 sm_103a" (static storage). */
+const char* gbdct_version(void);
+
+/*
+ * Create a plan for one transform of shape dims[0] x ... x dims[ndim-1] on the
+ * current CUDA device (Algorithm 2 "Require": a real N1 x N2 matrix).  The
+ * plan precomputes every twiddle table in FP64 on the device and rounds it to
+ * FP32 (the paper's coefficients "fixed before the call", Section III-B), and
+ * allocates its workspace (gbdct_plan_workspace_bytes).
+ *   out   receives the plan handle (unchanged on error).
+ *   ndim  2 (3 returns GBDCT_ERR_UNSUPPORTED in this build).
+ *   dims  ndim sizes; each must be a power of two between 2 and 16384, else
+ *         GBDCT_ERR_UNSUPPORTED (dims <= 0 give GBDCT_ERR_INVALID_ARG).
+ *   kind  a gbdct_kind; dtype must be GBDCT_F32.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises the device.
+ */
+gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims,
+                               int kind, int dtype);
+
+/*
+ * As gbdct_plan_create, for `batch` independent transforms of the same shape
+ * stored back to back (batch >= 1); one exec call processes all of them in the
+ * same launches.  The workspace grows linearly with `batch`.
+ */
+gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_t* dims,
+                                       int64_t batch, int kind, int dtype);
+
+/*
+ * Forward transform.  `in` and `out` are device pointers to batch * prod(dims)
+ * float32 values, 16-byte aligned; in == out (in place) is allowed.  The call
+ * is asynchronous on `stream`; the caller keeps both buffers alive until the
+ * stream has passed the work.  Errors: INVALID_ARG (NULL or misaligned
+ * pointer, NULL plan), CUDA (launch failure).
+ */
+gbdct_status gbdct_exec_forward(gbdct_plan_t plan, const void* in, void* out, void* stream);
+
+/* Inverse transform; same contract as gbdct_exec_forward. */
+gbdct_status gbdct_exec_inverse(gbdct_plan_t plan, const void* in, void* out, void* stream);
+
+/* Bytes of device workspace owned by the plan (0 for a NULL plan). */
+size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan);
+
+/* Number of kernel launches one exec call issues (0 for a NULL plan). */
+int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
+
+/* Release the plan and its device memory.  NULL is accepted (no-op).  The
+ * caller must make sure no stream still uses the plan. */
+gbdct_status gbdct_plan_destroy(gbdct_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBDCT_H_ */

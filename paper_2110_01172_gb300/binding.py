@@ -1,0 +1,219 @@
+"""Thin ctypes binding of the C ABI in include/gbdct.h (argument marshalling only).
+
+Every transform step runs in the CUDA kernels of ``libgbdct.so``; this module
+only checks tensors, allocates outputs with PyTorch and passes raw device
+pointers and the current CUDA stream.  There is no CPU fallback: if the
+library is missing or fails to load, every entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_UNSUPPORTED = 2
+ERR_OOM = 3
+ERR_CUDA = 4
+ERR_TIMEOUT = 5
+
+KINDS = {"dct2": 0, "dst2": 1, "idct_idxst": 2, "idxst_idct": 3}
+F32 = 0
+
+HEADER = os.path.join(_build.ROOT, "include", "gbdct.h")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class GbdctError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_name(status)}")
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions declared in the C header (used by the ABI tests)."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbdct_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load (building first if needed) the in-tree CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if path is None:
+            path = _build.library_path()
+            if build_if_missing and _build.is_stale():
+                _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgbdct not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        c_i64p = ctypes.POINTER(ctypes.c_int64)
+        plan_p = ctypes.c_void_p
+        sigs = {
+            "gbdct_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "gbdct_version": (ctypes.c_char_p, []),
+            "gbdct_plan_create": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int, c_i64p,
+                                                 ctypes.c_int, ctypes.c_int]),
+            "gbdct_plan_create_batched": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int, c_i64p,
+                                                         ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
+            "gbdct_exec_forward": (ctypes.c_int, [plan_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+            "gbdct_exec_inverse": (ctypes.c_int, [plan_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+            "gbdct_plan_workspace_bytes": (ctypes.c_size_t, [plan_p]),
+            "gbdct_plan_launches_per_exec": (ctypes.c_int, [plan_p]),
+            "gbdct_plan_destroy": (ctypes.c_int, [plan_p]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().gbdct_status_string(int(status)).decode()
+    except Exception:  # library unavailable: still give a readable message
+        return f"status {status}"
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise GbdctError(status, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream, device):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A transform plan: twiddle tables and workspace resident on one GPU.
+
+    shape: (N1, N2) of one transform; batch: number of transforms stored back
+    to back; kind: "dct2" (forward DCT-II, inverse = exact inverse).
+    """
+
+    def __init__(self, shape, kind: str = "dct2", batch: int = 1, device=None):
+        torch = _torch()
+        lib = load()
+        if kind not in KINDS:
+            raise ValueError(f"unknown kind {kind!r}")
+        self.shape = tuple(int(s) for s in shape)
+        self.kind = kind
+        self.batch = int(batch)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        dims = (ctypes.c_int64 * len(self.shape))(*self.shape)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.gbdct_plan_create_batched(ctypes.byref(handle), len(self.shape), dims,
+                                                 self.batch, KINDS[kind], F32), "gbdct_plan_create")
+        self._h = handle
+        self._lib = lib
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.gbdct_plan_workspace_bytes(self._h))
+
+    @property
+    def launches_per_exec(self) -> int:
+        return int(self._lib.gbdct_plan_launches_per_exec(self._h))
+
+    def _prep(self, x, out):
+        torch = _torch()
+        want = ((self.batch,) if self.batch > 1 else ()) + self.shape
+        if x.dtype != torch.float32 or not x.is_cuda:
+            raise TypeError("expected a CUDA float32 tensor")
+        if tuple(x.shape) != want:
+            raise ValueError(f"expected shape {want}, got {tuple(x.shape)}")
+        if not x.is_contiguous():
+            x = x.contiguous()
+        if out is None:
+            out = torch.empty_like(x)
+        elif tuple(out.shape) != want or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 tensor of the input's shape")
+        return x, out
+
+    def forward(self, x, out=None, stream=None):
+        x, out = self._prep(x, out)
+        _check(self._lib.gbdct_exec_forward(self._h, ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()),
+                                            _stream_handle(stream, x.device)), "gbdct_exec_forward")
+        return out
+
+    def inverse(self, x, out=None, stream=None):
+        x, out = self._prep(x, out)
+        _check(self._lib.gbdct_exec_inverse(self._h, ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()),
+                                            _stream_handle(stream, x.device)), "gbdct_exec_inverse")
+        return out
+
+    def forward_ptr(self, in_ptr: int, out_ptr: int, stream_ptr: int = 0) -> int:
+        """Raw-pointer forward call (returns the status code, never raises)."""
+        return int(self._lib.gbdct_exec_forward(self._h, ctypes.c_void_p(in_ptr),
+                                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream_ptr)))
+
+    def inverse_ptr(self, in_ptr: int, out_ptr: int, stream_ptr: int = 0) -> int:
+        return int(self._lib.gbdct_exec_inverse(self._h, ctypes.c_void_p(in_ptr),
+                                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream_ptr)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gbdct_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plans: dict = {}
+
+
+def _cached_plan(shape, kind, batch, device):
+    key = (tuple(shape), kind, batch, device)
+    p = _plans.get(key)
+    if p is None:
+        p = Plan(shape, kind, batch, device)
+        _plans[key] = p
+    return p
+
+
+def _split(x):
+    if x.dim() == 2:
+        return tuple(x.shape), 1
+    if x.dim() == 3:
+        return tuple(x.shape[1:]), int(x.shape[0])
+    raise ValueError("expected a 2D tensor or a batch of 2D tensors")
+
+
+def dct2(x, out=None):
+    """2D DCT-II (unnormalised) of a CUDA float32 (N1, N2) or (B, N1, N2) tensor."""
+    shape, batch = _split(x)
+    return _cached_plan(shape, "dct2", batch, x.device).forward(x, out)
+
+
+def idct2(x, out=None):
+    """Exact inverse of ``dct2`` (2/N-scaled DCT-III per axis)."""
+    shape, batch = _split(x)
+    return _cached_plan(shape, "dct2", batch, x.device).inverse(x, out)

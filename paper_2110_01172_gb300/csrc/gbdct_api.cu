@@ -1,0 +1,283 @@
+// gbdct_api.cu - plans, FP64 twiddle generation and the C ABI (include/gbdct.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include <new>
+
+#include "../../include/gbdct.h"
+#include "dct2d_launch.cuh"
+
+using gbdct::Dct2dArgs;
+
+struct gbdct_plan_s {
+  int ndim;
+  int64_t dims[3];
+  int64_t batch;
+  int kind;
+  int device;
+  int n1, n2, lg1, lg2;
+  float2* tables;   // one allocation holding every twiddle table
+  size_t table_elems;
+  float2* work;     // half-spectrum workspace, batch * (N1/2) * N2 complex
+  size_t work_bytes;
+  Dct2dArgs args;   // pointers and sizes shared by all passes
+  int b_cols, b_rows;  // sequences per CTA of the column and row passes
+};
+
+namespace {
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+// Stage twiddles of the Stockham FFT of length L (layout in fft_core.cuh):
+// entry (j-1)*NS + k of the stage starting at NS is exp(-2 pi i j k / (NS R)),
+// evaluated in FP64 from the exactly reduced integer j k mod (NS R).
+__global__ void k_gen_stage_twiddles(float2* out, int L, int total) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int off = 0;
+  for (int ns = 1; ns < L; ns *= gbdct::stage_radix(L, ns)) {
+    const int R = gbdct::stage_radix(L, ns);
+    if (ns == 1) continue;
+    const int sz = (R - 1) * ns;
+    if (idx < off + sz) {
+      const int e = idx - off;
+      const long long j = e / ns + 1, k = e % ns;
+      const long long M = (long long)ns * R;
+      const long long m = (j * k) % M;
+      double sn, cs;
+      sincospi(-2.0 * (double)m / (double)M, &sn, &cs);
+      out[idx] = make_float2((float)cs, (float)sn);
+      return;
+    }
+    off += sz;
+  }
+}
+
+// DCT twiddles (Section III-B, Eq. s-t: a = e^{-i pi n1/2N1}, b = e^{-i pi n2/2N2}):
+//   fa[k] = a_k,                      k in [0, N1/2]
+//   fb[k] = b_k / 2,                  k in [0, N2)      (the 1/2 of the combine)
+//   ia[k] = conj(a_k) / (N1 N2),      k in [0, N1/2]    (inverse DFT scale folded in)
+//   ib[k] = conj(b_k),                k in [0, N2)
+__global__ void k_gen_dct_tables(float2* fa, float2* fb, float2* ia, float2* ib, int n1, int n2) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx <= n1 / 2) {
+    double sn, cs;
+    sincospi((double)idx / (2.0 * (double)n1), &sn, &cs);
+    fa[idx] = make_float2((float)cs, (float)(-sn));
+    const double sc = 1.0 / ((double)n1 * (double)n2);
+    ia[idx] = make_float2((float)(cs * sc), (float)(sn * sc));
+  }
+  if (idx < n2) {
+    double sn, cs;
+    sincospi((double)idx / (2.0 * (double)n2), &sn, &cs);
+    fb[idx] = make_float2((float)(0.5 * cs), (float)(-0.5 * sn));
+    ib[idx] = make_float2((float)cs, (float)sn);
+  }
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+gbdct_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return GBDCT_OK;
+  if (e == cudaErrorMemoryAllocation) return GBDCT_ERR_OOM;
+  return GBDCT_ERR_CUDA;
+}
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool switched = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      switched = (cudaSetDevice(dev) == cudaSuccess);
+    }
+  }
+  ~DeviceGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
+
+void free_plan(gbdct_plan_s* p) {
+  if (!p) return;
+  if (p->tables) cudaFree(p->tables);
+  if (p->work) cudaFree(p->work);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gbdct_status_string(gbdct_status status) {
+  switch (status) {
+    case GBDCT_OK: return "GBDCT_OK";
+    case GBDCT_ERR_INVALID_ARG: return "GBDCT_ERR_INVALID_ARG";
+    case GBDCT_ERR_UNSUPPORTED: return "GBDCT_ERR_UNSUPPORTED";
+    case GBDCT_ERR_OOM: return "GBDCT_ERR_OOM";
+    case GBDCT_ERR_CUDA: return "GBDCT_ERR_CUDA";
+    case GBDCT_ERR_TIMEOUT: return "GBDCT_ERR_TIMEOUT";
+  }
+  return "GBDCT_ERR_UNKNOWN";
+}
+
+const char* gbdct_version(void) { return "gbdct 0.1.0 sm_103a"; }
+
+gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_t* dims,
+                                       int64_t batch, int kind, int dtype) {
+  if (!out || !dims || batch < 1) return GBDCT_ERR_INVALID_ARG;
+  if (ndim < 1 || ndim > 3) return GBDCT_ERR_INVALID_ARG;
+  for (int i = 0; i < ndim; ++i)
+    if (dims[i] <= 0) return GBDCT_ERR_INVALID_ARG;
+  if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
+  if (dtype != GBDCT_F32) return GBDCT_ERR_UNSUPPORTED;
+  if (ndim != 2) return GBDCT_ERR_UNSUPPORTED;
+  if (kind != GBDCT_DCT2) return GBDCT_ERR_UNSUPPORTED;
+  for (int i = 0; i < ndim; ++i) {
+    if (!is_pow2(dims[i])) return GBDCT_ERR_UNSUPPORTED;
+    const int lg = ilog2(dims[i]);
+    if (lg < gbdct::kMinLog2 || lg > gbdct::kMaxLog2) return GBDCT_ERR_UNSUPPORTED;
+  }
+  if (batch > 65535) return GBDCT_ERR_UNSUPPORTED;
+
+  gbdct_plan_s* p = new (std::nothrow) gbdct_plan_s();
+  if (!p) return GBDCT_ERR_OOM;
+  p->ndim = ndim;
+  for (int i = 0; i < 3; ++i) p->dims[i] = i < ndim ? dims[i] : 1;
+  p->batch = batch;
+  p->kind = kind;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return GBDCT_ERR_CUDA;
+  }
+  const int n1 = (int)dims[0], n2 = (int)dims[1];
+  p->n1 = n1;
+  p->n2 = n2;
+  p->lg1 = ilog2(n1);
+  p->lg2 = ilog2(n2);
+
+  // Table layout, each block padded to 2 float2 (16 B).
+  const size_t t1 = round_up(gbdct::tw_size(n1) + 1, 2);
+  const size_t t2 = round_up(gbdct::tw_size(n2) + 1, 2);
+  const size_t ta = round_up(n1 / 2 + 1, 2);
+  const size_t tb = round_up(n2, 2);
+  p->table_elems = t1 + t2 + 2 * ta + 2 * tb;
+  cudaError_t e = cudaMalloc(&p->tables, p->table_elems * sizeof(float2));
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  float2* tw1 = p->tables;
+  float2* tw2 = tw1 + t1;
+  float2* fa = tw2 + t2;
+  float2* ia = fa + ta;
+  float2* fb = ia + ta;
+  float2* ib = fb + tb;
+
+  p->work_bytes = (size_t)batch * (size_t)(n1 / 2) * (size_t)n2 * sizeof(float2);
+  e = cudaMalloc(&p->work, p->work_bytes);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+
+  const int tot1 = gbdct::tw_size(n1), tot2 = gbdct::tw_size(n2);
+  if (tot1 > 0) k_gen_stage_twiddles<<<(tot1 + 255) / 256, 256>>>(tw1, n1, tot1);
+  if (tot2 > 0) k_gen_stage_twiddles<<<(tot2 + 255) / 256, 256>>>(tw2, n2, tot2);
+  const int nt = (n1 / 2 + 1 > n2) ? (n1 / 2 + 1) : n2;
+  k_gen_dct_tables<<<(nt + 255) / 256, 256>>>(fa, fb, ia, ib, n1, n2);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+
+  Dct2dArgs& a = p->args;
+  a.n1 = n1;
+  a.n2 = n2;
+  a.in_bstride = (long long)n1 * n2;
+  a.out_bstride = (long long)n1 * n2;
+  a.work_bstride = (long long)(n1 / 2) * n2;
+  a.work = p->work;
+  a.tw1 = tw1;
+  a.tw2 = tw2;
+  a.fa = fa;
+  a.fb = fb;
+  a.ia = ia;
+  a.ib = ib;
+  p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
+  p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
+
+  // Raise the dynamic shared-memory limit of the four kernels once.
+  Dct2dArgs ac = a, ar = a;
+  ac.seq_per_cta = p->b_cols;
+  ar.seq_per_cta = p->b_rows;
+  dim3 g(1, 1);
+  e = gbdct::run_fwd_cols(p->lg1, ac, g, 0, true);
+  if (e == cudaSuccess) e = gbdct::run_inv_cols(p->lg1, ac, g, 0, true);
+  if (e == cudaSuccess) e = gbdct::run_fwd_rows(p->lg2, ar, g, 0, true);
+  if (e == cudaSuccess) e = gbdct::run_inv_rows(p->lg2, ar, g, 0, true);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  *out = p;
+  return GBDCT_OK;
+}
+
+gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims, int kind,
+                               int dtype) {
+  return gbdct_plan_create_batched(out, ndim, dims, 1, kind, dtype);
+}
+
+static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stream, bool inverse) {
+  if (!p || !in || !out) return GBDCT_ERR_INVALID_ARG;
+  if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return GBDCT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Dct2dArgs a = p->args;
+  a.in = static_cast<const float*>(in);
+  a.out = static_cast<float*>(out);
+  const int batch = (int)p->batch;
+  Dct2dArgs ac = a, ar = a;
+  ac.seq_per_cta = p->b_cols;
+  ar.seq_per_cta = p->b_rows;
+  const dim3 gc((p->n2 / 2) / p->b_cols, batch);
+  const dim3 gr((p->n1 / 2) / p->b_rows, batch);
+  cudaError_t e;
+  if (!inverse) {
+    e = gbdct::run_fwd_cols(p->lg1, ac, gc, s, false);
+    if (e == cudaSuccess) e = gbdct::run_fwd_rows(p->lg2, ar, gr, s, false);
+  } else {
+    e = gbdct::run_inv_rows(p->lg2, ar, gr, s, false);
+    if (e == cudaSuccess) e = gbdct::run_inv_cols(p->lg1, ac, gc, s, false);
+  }
+  return cuda_status(e);
+}
+
+gbdct_status gbdct_exec_forward(gbdct_plan_t plan, const void* in, void* out, void* stream) {
+  return exec2d(plan, in, out, stream, false);
+}
+
+gbdct_status gbdct_exec_inverse(gbdct_plan_t plan, const void* in, void* out, void* stream) {
+  return exec2d(plan, in, out, stream, true);
+}
+
+size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_bytes : 0; }
+
+int gbdct_plan_launches_per_exec(gbdct_plan_t plan) { return plan ? 2 : 0; }
+
+gbdct_status gbdct_plan_destroy(gbdct_plan_t plan) {
+  if (!plan) return GBDCT_OK;
+  DeviceGuard guard(plan->device);
+  free_plan(plan);
+  return GBDCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every declared symbol (CPU only).
+
+No call here touches a GPU: only argument validation that the library
+performs before any CUDA call is exercised.
+"""
+
+import ctypes
+
+import pytest
+
+from paper_2110_01172_gb300 import binding, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_expected_entry_points():
+    names = binding.declared_functions()
+    for n in ("gbdct_plan_create", "gbdct_plan_create_batched", "gbdct_exec_forward",
+              "gbdct_exec_inverse", "gbdct_plan_destroy", "gbdct_plan_workspace_bytes",
+              "gbdct_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in binding.declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    assert lib.gbdct_status_string(0) == b"GBDCT_OK"
+    assert lib.gbdct_status_string(2) == b"GBDCT_ERR_UNSUPPORTED"
+    assert lib.gbdct_status_string(99) == b"GBDCT_ERR_UNKNOWN"
+    assert b"sm_103a" in lib.gbdct_version()
+
+
+def _create(lib, dims, ndim=None, kind=0, dtype=0, batch=1):
+    arr = (ctypes.c_int64 * max(1, len(dims)))(*dims)
+    h = ctypes.c_void_p()
+    st = lib.gbdct_plan_create_batched(ctypes.byref(h), len(dims) if ndim is None else ndim,
+                                       arr, batch, kind, dtype)
+    return st, h
+
+
+@pytest.mark.parametrize("dims,ndim,kind,dtype,batch,expect", [
+    ((0, 8), None, 0, 0, 1, binding.ERR_INVALID_ARG),       # dim <= 0
+    ((8, -4), None, 0, 0, 1, binding.ERR_INVALID_ARG),
+    ((8, 8), 4, 0, 0, 1, binding.ERR_INVALID_ARG),           # rank out of range
+    ((8, 8), 0, 0, 0, 1, binding.ERR_INVALID_ARG),
+    ((8, 8), None, 9, 0, 1, binding.ERR_INVALID_ARG),        # unknown kind
+    ((8, 8), None, 0, 0, 0, binding.ERR_INVALID_ARG),        # batch < 1
+    ((8, 8), None, 0, 3, 1, binding.ERR_UNSUPPORTED),        # dtype
+    ((12, 8), None, 0, 0, 1, binding.ERR_UNSUPPORTED),       # not a power of two
+    ((1, 8), None, 0, 0, 1, binding.ERR_UNSUPPORTED),        # below the smallest size
+    ((8, 32768), None, 0, 0, 1, binding.ERR_UNSUPPORTED),    # above the largest size
+])
+def test_plan_create_rejects_before_touching_the_gpu(lib, dims, ndim, kind, dtype, batch, expect):
+    st, h = _create(lib, dims, ndim, kind, dtype, batch)
+    assert st == expect
+    assert not h.value
+
+
+def test_null_handles(lib):
+    assert lib.gbdct_exec_forward(None, None, None, None) == binding.ERR_INVALID_ARG
+    assert lib.gbdct_exec_inverse(None, None, None, None) == binding.ERR_INVALID_ARG
+    assert lib.gbdct_plan_destroy(None) == binding.OK
+    assert lib.gbdct_plan_workspace_bytes(None) == 0
+    assert lib.gbdct_plan_launches_per_exec(None) == 0
+    h = ctypes.c_void_p()
+    assert lib.gbdct_plan_create(ctypes.byref(h), 2, None, 0, 0) == binding.ERR_INVALID_ARG
+    assert lib.gbdct_plan_create(None, 2, (ctypes.c_int64 * 2)(8, 8), 0, 0) == binding.ERR_INVALID_ARG

@@ -1,0 +1,143 @@
+"""GPU parity of the 2D DCT-II / inverse against the FP64 oracle (needs a GB300).
+
+Acceptance (FP32): relative L2 error <= 1e-5 and max abs error <= 1e-4 max|X|
+against the oracle on the same float32 inputs.  Full comparisons run at sizes
+the oracle finishes in seconds (several FFT tiles, every power-of-two pair up
+to 128, rectangular up to 2048); the benchmark's 4096^2 and the largest sizes
+are checked on sampled entries computed one by one, plus the round trip.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_01172_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+MAX_ABS = 1e-4
+
+
+def _plan(shape, batch=1):
+    from paper_2110_01172_gb300 import Plan
+    return Plan(shape, "dct2", batch=batch)
+
+
+def check(got, ref, rel=REL_L2, mabs=MAX_ABS):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    mx = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+    assert err <= rel and mx <= mabs, f"rel-L2 {err:.3e}, max-abs/max {mx:.3e}"
+    return err
+
+
+def run_forward_inverse(x, batch=1):
+    shape = x.shape[-2:]
+    plan = _plan(shape, batch)
+    xd = torch.from_numpy(x).cuda()
+    X = plan.forward(xd)
+    torch.cuda.synchronize()
+    Xh = X.cpu().numpy()
+    Y = plan.inverse(X)
+    torch.cuda.synchronize()
+    return Xh, Y.cpu().numpy()
+
+
+def test_config_256_seed0():
+    # the 256x256 U[-1,1] seed-0 configuration, forward and inverse
+    x = inputs.uniform((256, 256), seed=0)
+    X, y = run_forward_inverse(x)
+    check(X, oracle.dct2_2d(x))
+    check(y, oracle.idct2_2d(X))
+    check(y, x.astype(np.float64), rel=1e-5, mabs=1e-4)
+
+
+SIZES = [2, 4, 8, 16, 32, 64, 128]
+
+
+@pytest.mark.parametrize("n1", SIZES)
+@pytest.mark.parametrize("n2", SIZES)
+def test_all_small_power_of_two_pairs(n1, n2):
+    x = inputs.uniform((n1, n2), seed=n1 * 1000 + n2)
+    X, y = run_forward_inverse(x)
+    check(X, oracle.dct2_2d(x))
+    check(y, oracle.idct2_2d(X))
+
+
+@pytest.mark.parametrize("shape", [(1024, 256), (256, 2048), (2048, 2), (2, 2048), (512, 1024),
+                                   (1024, 1024)])
+def test_rectangular(shape):
+    x = inputs.uniform(shape, seed=7)
+    X, y = run_forward_inverse(x)
+    check(X, oracle.dct2_2d(x))
+    check(y, oracle.idct2_2d(X))
+
+
+@pytest.mark.parametrize("shape", [(256, 512), (1024, 1024)])
+def test_smooth_gaussian_bump_fields(shape):
+    x = inputs.gaussian_bumps(shape, seed=3)
+    X, y = run_forward_inverse(x)
+    check(X, oracle.dct2_2d(x))
+    check(y, oracle.idct2_2d(X))
+
+
+def test_batched_matches_per_transform_oracle():
+    xs = np.stack([inputs.uniform((64, 128), seed=s) for s in range(3)])
+    X, y = run_forward_inverse(xs, batch=3)
+    for b in range(3):
+        check(X[b], oracle.dct2_2d(xs[b]))
+        check(y[b], oracle.idct2_2d(X[b]))
+
+
+def test_in_place():
+    x = inputs.uniform((128, 64), seed=9)
+    plan = _plan(x.shape)
+    xd = torch.from_numpy(x).cuda()
+    plan.forward(xd, out=xd)
+    torch.cuda.synchronize()
+    X = xd.cpu().numpy()
+    check(X, oracle.dct2_2d(x))
+    plan.inverse(xd, out=xd)
+    torch.cuda.synchronize()
+    check(xd.cpu().numpy(), oracle.idct2_2d(X))
+
+
+def _sample_indices(n1, n2, count, seed):
+    rng = np.random.default_rng(seed)
+    k1 = list(rng.integers(0, n1, count)) + [0, 0, n1 - 1, n1 // 2, n1 // 2, 1, n1 - 1]
+    k2 = list(rng.integers(0, n2, count)) + [0, n2 - 1, 0, n2 // 2, 0, n2 // 2, n2 - 1]
+    return np.array(k1), np.array(k2)
+
+
+@pytest.mark.parametrize("shape", [(4096, 4096), (8192, 8192), (2048, 4096), (1024, 8192),
+                                   (16384, 1024), (2, 16384)])
+def test_large_sizes_sampled_entries_and_round_trip(shape):
+    n1, n2 = shape
+    x = inputs.uniform(shape, seed=0)
+    X, y = run_forward_inverse(x)
+    k1, k2 = _sample_indices(n1, n2, 48, seed=n1 + n2)
+    ref = oracle.dct2_2d_entries(x, k1, k2)
+    got = X[k1, k2].astype(np.float64)
+    scale = np.abs(X).max()
+    assert np.abs(got - ref).max() <= MAX_ABS * scale
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= REL_L2
+    # inverse: sampled entries of the exact inverse of the float32 spectrum
+    j1, j2 = _sample_indices(n1, n2, 16, seed=n1 * 3 + n2)
+    ref_inv = oracle.idct2_2d_entries(X, j1, j2)
+    got_inv = y[j1, j2].astype(np.float64)
+    assert np.abs(got_inv - ref_inv).max() <= MAX_ABS * np.abs(y).max()
+    # round trip over the whole array
+    check(y, x.astype(np.float64))
+
+
+def test_bad_pointers_are_rejected():
+    from paper_2110_01172_gb300 import binding
+    plan = _plan((64, 64))
+    buf = torch.zeros(64 * 64 + 4, device="cuda")
+    base = buf.data_ptr()
+    assert plan.forward_ptr(base + 4, base) == binding.ERR_INVALID_ARG
+    assert plan.inverse_ptr(base, base + 8) == binding.ERR_INVALID_ARG
+    assert plan.forward_ptr(0, base) == binding.ERR_INVALID_ARG
