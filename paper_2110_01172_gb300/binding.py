@@ -70,6 +70,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_exec_inverse": (ctypes.c_int, [plan_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
             "gbdct_plan_workspace_bytes": (ctypes.c_size_t, [plan_p]),
             "gbdct_plan_launches_per_exec": (ctypes.c_int, [plan_p]),
+            "gbdct_plan_kernel_family": (ctypes.c_char_p, [plan_p]),
             "gbdct_plan_destroy": (ctypes.c_int, [plan_p]),
         }
         for name, (res, args) in sigs.items():
@@ -132,6 +133,10 @@ class Plan:
     @property
     def workspace_bytes(self) -> int:
         return int(self._lib.gbdct_plan_workspace_bytes(self._h))
+
+    @property
+    def family(self) -> str:
+        return self._lib.gbdct_plan_kernel_family(self._h).decode()
 
     @property
     def launches_per_exec(self) -> int:

@@ -73,7 +73,7 @@ k_fwd_cols(Dct2dArgs a) {
   extern __shared__ float4 smem_f4[];
   float2* sm = reinterpret_cast<float2*>(smem_f4);
   constexpr int TPS = fft_tps(L);
-  constexpr int LP = pad_len(L);
+  constexpr int LP = pad_len<float2>(L);
   const int B = a.seq_per_cta;
   const int N2 = a.n2;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -84,7 +84,7 @@ k_fwd_cols(Dct2dArgs a) {
   for (int i = tid; i < L * B; i += nthr) {
     const int b = i % B, r = i / B;
     const float2 z = __ldg(reinterpret_cast<const float2*>(x + (long long)r * N2 + 2 * (p0 + b)));
-    sm[b * LP + pidx(reorder_dst(r, L))] = z;
+    sm[b * LP + pidx<float2>(reorder_dst(r, L))] = z;
   }
   __syncthreads();
   cta_fft<L, false>(sm + (tid / TPS) * LP, tid % TPS, a.tw1);
@@ -97,13 +97,13 @@ k_fwd_cols(Dct2dArgs a) {
     const int p = p0 + b;
     float2 u, w;
     if (k == 0) {
-      const float2 z0 = s[pidx(0)];
-      const float2 zh = s[pidx(L / 2)];
+      const float2 z0 = s[pidx<float2>(0)];
+      const float2 zh = s[pidx<float2>(L / 2)];
       u = make_float2(z0.x, zh.x);  // U[0], U[L/2] are real: packed re/im
       w = make_float2(z0.y, zh.y);
     } else {
-      const float2 zk = s[pidx(k)];
-      const float2 zm = s[pidx(L - k)];
+      const float2 zk = s[pidx<float2>(k)];
+      const float2 zm = s[pidx<float2>(L - k)];
       u = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
       w = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
     }
@@ -121,7 +121,7 @@ k_fwd_rows(Dct2dArgs a) {
   extern __shared__ float4 smem_f4[];
   float2* sm = reinterpret_cast<float2*>(smem_f4);
   constexpr int TPS = fft_tps(L);
-  constexpr int LP = pad_len(L);
+  constexpr int LP = pad_len<float2>(L);
   const int B = a.seq_per_cta;
   const int N1 = a.n1;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -131,7 +131,7 @@ k_fwd_rows(Dct2dArgs a) {
 
   for (int i = tid; i < L * B; i += nthr) {
     const int b = i / L, c = i % L;
-    sm[b * LP + pidx(c)] = W[(long long)(r0 + b) * L + c];
+    sm[b * LP + pidx<float2>(c)] = W[(long long)(r0 + b) * L + c];
   }
   __syncthreads();
   cta_fft<L, false>(sm + (tid / TPS) * LP, tid % TPS, a.tw2);
@@ -141,8 +141,8 @@ k_fwd_rows(Dct2dArgs a) {
     const int b = i / H, k2 = i % H;
     const int k1 = r0 + b;
     const float2* s = sm + b * LP;
-    const float2 Y = s[pidx(k2)];
-    const float2 Ym = s[pidx((L - k2) & (L - 1))];
+    const float2 Y = s[pidx<float2>(k2)];
+    const float2 Ym = s[pidx<float2>((L - k2) & (L - 1))];
     const float2 bt = __ldg(a.fb + k2);  // b_k2 / 2
     const bool mirror = (k2 != 0) && (k2 != L / 2);
     if (k1 == 0) {
@@ -189,7 +189,7 @@ k_inv_rows(Dct2dArgs a) {
   extern __shared__ float4 smem_f4[];
   float2* sm = reinterpret_cast<float2*>(smem_f4);
   constexpr int TPS = fft_tps(L);
-  constexpr int LP = pad_len(L);
+  constexpr int LP = pad_len<float2>(L);
   const int B = a.seq_per_cta;
   const int N1 = a.n1;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -218,11 +218,11 @@ k_inv_rows(Dct2dArgs a) {
       // V(0,k2) = a0 b [c01 - i c02];  V(h,k2) = ah b [(ch1-ch2) - i(ch1+ch2)]
       const float2 v0 = cmul(a0, cmul(bk, make_float2(c01, -c02)));
       const float2 vh = cmul(ah, cmul(bk, make_float2(ch1 - ch2, -(ch1 + ch2))));
-      s[pidx(k2)] = make_float2(v0.x - vh.y, v0.y + vh.x);  // V(0) + i V(h)
+      s[pidx<float2>(k2)] = make_float2(v0.x - vh.y, v0.y + vh.x);  // V(0) + i V(h)
       if (mirror) {
         const float2 w0 = cmul(a0, cmul(bm, make_float2(c02, -c01)));
         const float2 wh = cmul(ah, cmul(bm, make_float2(ch2 - ch1, -(ch2 + ch1))));
-        s[pidx(km)] = make_float2(w0.x - wh.y, w0.y + wh.x);
+        s[pidx<float2>(km)] = make_float2(w0.x - wh.y, w0.y + wh.x);
       }
     } else {
       const float* ca = C + (long long)k1 * L;
@@ -234,8 +234,8 @@ k_inv_rows(Dct2dArgs a) {
       const float2 av = __ldg(a.ia + k1);
       // V(k1,k2)    = a b [(c1 - c2) - i (c3 + c4)]
       // V(k1,N2-k2) = a b'[(c4 - c3) - i (c2 + c1)]
-      s[pidx(k2)] = cmul(av, cmul(bk, make_float2(c1 - c2, -(c3 + c4))));
-      if (mirror) s[pidx(km)] = cmul(av, cmul(bm, make_float2(c4 - c3, -(c2 + c1))));
+      s[pidx<float2>(k2)] = cmul(av, cmul(bk, make_float2(c1 - c2, -(c3 + c4))));
+      if (mirror) s[pidx<float2>(km)] = cmul(av, cmul(bm, make_float2(c4 - c3, -(c2 + c1))));
     }
   }
   __syncthreads();
@@ -243,7 +243,7 @@ k_inv_rows(Dct2dArgs a) {
 
   for (int i = tid; i < L * B; i += nthr) {
     const int b = i / L, c = i % L;
-    W[(long long)(r0 + b) * L + c] = sm[b * LP + pidx(c)];
+    W[(long long)(r0 + b) * L + c] = sm[b * LP + pidx<float2>(c)];
   }
 }
 
@@ -256,7 +256,7 @@ k_inv_cols(Dct2dArgs a) {
   extern __shared__ float4 smem_f4[];
   float2* sm = reinterpret_cast<float2*>(smem_f4);
   constexpr int TPS = fft_tps(L);
-  constexpr int LP = pad_len(L);
+  constexpr int LP = pad_len<float2>(L);
   const int B = a.seq_per_cta;
   const int N2 = a.n2;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -271,12 +271,12 @@ k_inv_cols(Dct2dArgs a) {
     const float2 wp = W[(long long)k * N2 + p];
     const float2 wq = W[(long long)k * N2 + (N2 - 1 - p)];
     if (k == 0) {
-      s[pidx(0)] = make_float2(wp.x, wq.x);
-      s[pidx(L / 2)] = make_float2(wp.y, wq.y);
+      s[pidx<float2>(0)] = make_float2(wp.x, wq.x);
+      s[pidx<float2>(L / 2)] = make_float2(wp.y, wq.y);
     } else {
       // Z(k) = U(k,p) + i U(k,q);  Z(L-k) = conj U(k,p) + i conj U(k,q)
-      s[pidx(k)] = make_float2(wp.x - wq.y, wp.y + wq.x);
-      s[pidx(L - k)] = make_float2(wp.x + wq.y, wq.x - wp.y);
+      s[pidx<float2>(k)] = make_float2(wp.x - wq.y, wp.y + wq.x);
+      s[pidx<float2>(L - k)] = make_float2(wp.x + wq.y, wq.x - wp.y);
     }
   }
   __syncthreads();
@@ -284,7 +284,7 @@ k_inv_cols(Dct2dArgs a) {
 
   for (int i = tid; i < L * B; i += nthr) {
     const int b = i % B, n = i / B;
-    const float2 z = sm[b * LP + pidx(n)];
+    const float2 z = sm[b * LP + pidx<float2>(n)];
     *reinterpret_cast<float2*>(x + (long long)reorder_src(n, L) * N2 + 2 * (p0 + b)) = z;
   }
 }

@@ -9,6 +9,9 @@
 #include <cuda_runtime.h>
 
 #include "dct2d_kernels.cuh"
+#include "dct2d_pair_kernels.cuh"
+#include "dct2d_r64_kernels.cuh"
+#include "dct2d_fs_kernels.cuh"
 
 namespace gbdct {
 
@@ -17,7 +20,7 @@ constexpr int kMaxLog2 = 14;
 
 inline int seq_threads(int L, int seq_per_cta) { return seq_per_cta * fft_tps(L); }
 inline size_t seq_smem_bytes(int L, int seq_per_cta) {
-  return (size_t)seq_per_cta * (size_t)pad_len(L) * sizeof(float2);
+  return (size_t)seq_per_cta * (size_t)pad_len<float2>(L) * sizeof(float2);
 }
 
 // Sequences per CTA: enough to give the CTA ~512 threads (1024 at L = 16384,
@@ -34,6 +37,54 @@ cudaError_t run_fwd_cols(int log2L, const Dct2dArgs& a, dim3 grid, cudaStream_t 
 cudaError_t run_fwd_rows(int log2L, const Dct2dArgs& a, dim3 grid, cudaStream_t s, bool prepare);
 cudaError_t run_inv_rows(int log2L, const Dct2dArgs& a, dim3 grid, cudaStream_t s, bool prepare);
 cudaError_t run_inv_cols(int log2L, const Dct2dArgs& a, dim3 grid, cudaStream_t s, bool prepare);
+
+// Two-sequence (float4) passes for 16 <= L <= 8192: `npairs` sequence pairs
+// per transform, `batch` transforms (grid.y).
+cudaError_t run_fwd_cols2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
+cudaError_t run_fwd_rows2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
+cudaError_t run_inv_rows2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
+cudaError_t run_inv_cols2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
+// Radix-64 passes for L in {4096, 8192}: `nitems` CTAs (two sequences each).
+cudaError_t run_fwd_cols_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
+cudaError_t run_fwd_rows_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
+cudaError_t run_inv_rows_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
+cudaError_t run_inv_cols_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
+constexpr int kR64MinLog2 = 12;
+constexpr int kR64MaxLog2 = 13;
+
+template <int L>
+cudaError_t launch_r64(void (*kern)(Dct2dArgs), const Dct2dArgs& a, int nitems, int batch, cudaStream_t s,
+                       bool prepare) {
+  using G = R64Geom<L>;
+  if (prepare) {
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+  }
+  kern<<<dim3(nitems, batch), G::THREADS, G::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Four-step family: N1 in {1024, 2048, 4096}, N2 in {4096, 8192}.  One call
+// launches the whole forward (C1, C2, row pass) or inverse (row pass, C2', C1').
+cudaError_t run_fs(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, const float2* fstw, int batch,
+                   cudaStream_t s, bool prepare);
+constexpr int kFsMinLog2N1 = 10, kFsMaxLog2N1 = 12, kFsMinLog2N2 = 12, kFsMaxLog2N2 = 13;
+
+constexpr int kPairMinLog2 = 4;
+constexpr int kPairMaxLog2 = 13;
+
+template <int L>
+cudaError_t launch_pair(void (*kern)(Dct2dArgs), const Dct2dArgs& a, int npairs, int batch, cudaStream_t s,
+                        bool prepare) {
+  using G = PairGeom<L>;
+  if (prepare) {
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+  }
+  const dim3 grid((npairs + G::PB - 1) / G::PB, batch);
+  kern<<<grid, G::THREADS, G::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
 
 template <int L>
 cudaError_t launch_pass(void (*kern)(Dct2dArgs), const Dct2dArgs& a, dim3 grid, cudaStream_t s,
@@ -69,4 +120,32 @@ cudaError_t launch_pass(void (*kern)(Dct2dArgs), const Dct2dArgs& a, dim3 grid, 
       case 14: return launch_pass<16384>(KERN<16384>, a, grid, s, prep);                  \
       default: return cudaErrorInvalidValue;                                              \
     }                                                                                     \
+  }
+
+// Defines run_<NAME>(log2L, ...) for the two-sequence kernels, L = 16 .. 8192.
+#define GBDCT_DEFINE_PAIR_RUNNER(NAME, KERN)                                                        \
+  cudaError_t NAME(int log2L, const Dct2dArgs& a, int np, int nb, cudaStream_t s, bool prep) {      \
+    switch (log2L) {                                                                                \
+      case 4: return launch_pair<16>(KERN<16>, a, np, nb, s, prep);                                 \
+      case 5: return launch_pair<32>(KERN<32>, a, np, nb, s, prep);                                 \
+      case 6: return launch_pair<64>(KERN<64>, a, np, nb, s, prep);                                 \
+      case 7: return launch_pair<128>(KERN<128>, a, np, nb, s, prep);                               \
+      case 8: return launch_pair<256>(KERN<256>, a, np, nb, s, prep);                               \
+      case 9: return launch_pair<512>(KERN<512>, a, np, nb, s, prep);                               \
+      case 10: return launch_pair<1024>(KERN<1024>, a, np, nb, s, prep);                            \
+      case 11: return launch_pair<2048>(KERN<2048>, a, np, nb, s, prep);                            \
+      case 12: return launch_pair<4096>(KERN<4096>, a, np, nb, s, prep);                            \
+      case 13: return launch_pair<8192>(KERN<8192>, a, np, nb, s, prep);                            \
+      default: return cudaErrorInvalidValue;                                                        \
+    }                                                                                               \
+  }
+
+// Defines run_<NAME>(log2L, ...) for the radix-64 kernels, L = 4096, 8192.
+#define GBDCT_DEFINE_R64_RUNNER(NAME, KERN)                                                         \
+  cudaError_t NAME(int log2L, const Dct2dArgs& a, int ni, int nb, cudaStream_t s, bool prep) {      \
+    switch (log2L) {                                                                                \
+      case 12: return launch_r64<4096>(KERN<4096>, a, ni, nb, s, prep);                             \
+      case 13: return launch_r64<8192>(KERN<8192>, a, ni, nb, s, prep);                             \
+      default: return cudaErrorInvalidValue;                                                        \
+    }                                                                                               \
   }

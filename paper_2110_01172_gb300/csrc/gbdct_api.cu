@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <new>
 
@@ -23,9 +24,19 @@ struct gbdct_plan_s {
   size_t work_bytes;
   Dct2dArgs args;   // pointers and sizes shared by all passes
   int b_cols, b_rows;  // sequences per CTA of the column and row passes
+  int family;          // kernel family: FAM_SEQ, FAM_PAIR, FAM_R64 or FAM_FS
+  float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS only)
+  int pmax;            // points per thread of the stage structure (twiddle layout)
 };
 
 namespace {
+
+// Kernel families (all compute the same transform; chosen by size):
+//   FAM_FS   four-step column FFTs + radix-64 rows, N1 in {1024..4096}, N2 in {4096, 8192}
+//   FAM_R64  radix-64 register FFTs, N1 and N2 in {4096, 8192}
+//   FAM_PAIR two interleaved sequences per thread, 16 <= N1, N2 <= 8192
+//   FAM_SEQ  one sequence per thread group, any supported size
+enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_R64 = 2, FAM_FS = 3 };
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int64_t v) {
@@ -37,12 +48,12 @@ int ilog2(int64_t v) {
 // Stage twiddles of the Stockham FFT of length L (layout in fft_core.cuh):
 // entry (j-1)*NS + k of the stage starting at NS is exp(-2 pi i j k / (NS R)),
 // evaluated in FP64 from the exactly reduced integer j k mod (NS R).
-__global__ void k_gen_stage_twiddles(float2* out, int L, int total) {
+__global__ void k_gen_stage_twiddles(float2* out, int L, int pmax, int total) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   int off = 0;
-  for (int ns = 1; ns < L; ns *= gbdct::stage_radix(L, ns)) {
-    const int R = gbdct::stage_radix(L, ns);
+  for (int ns = 1; ns < L; ns *= gbdct::stage_radix_p(L, ns, pmax)) {
+    const int R = gbdct::stage_radix_p(L, ns, pmax);
     if (ns == 1) continue;
     const int sz = (R - 1) * ns;
     if (idx < off + sz) {
@@ -79,6 +90,16 @@ __global__ void k_gen_dct_tables(float2* fa, float2* fb, float2* ia, float2* ib,
     fb[idx] = make_float2((float)(0.5 * cs), (float)(-0.5 * sn));
     ib[idx] = make_float2((float)cs, (float)sn);
   }
+}
+
+// Four-step twiddles W_N1^{n1a k1b} at n1a * B + k1b (n1a < A, k1b < B), FP64.
+__global__ void k_gen_fs_twiddles(float2* out, int n1, int A, int B) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= A * B) return;
+  const long long m = ((long long)(idx / B) * (idx % B)) % n1;
+  double sn, cs;
+  sincospi(-2.0 * (double)m / (double)n1, &sn, &cs);
+  out[idx] = make_float2((float)cs, (float)sn);
 }
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -161,12 +182,33 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   p->lg1 = ilog2(n1);
   p->lg2 = ilog2(n2);
 
+  const bool r64 = p->lg1 >= gbdct::kR64MinLog2 && p->lg1 <= gbdct::kR64MaxLog2 &&
+                   p->lg2 >= gbdct::kR64MinLog2 && p->lg2 <= gbdct::kR64MaxLog2;
+  const bool pair = p->lg1 >= gbdct::kPairMinLog2 && p->lg1 <= gbdct::kPairMaxLog2 &&
+                    p->lg2 >= gbdct::kPairMinLog2 && p->lg2 <= gbdct::kPairMaxLog2;
+  const bool fs = p->lg1 >= gbdct::kFsMinLog2N1 && p->lg1 <= gbdct::kFsMaxLog2N1 &&
+                  p->lg2 >= gbdct::kFsMinLog2N2 && p->lg2 <= gbdct::kFsMaxLog2N2;
+  // Default: the two-sequence family wherever it applies (fastest measured so
+  // far); the radix-64 and four-step families are opt-in below.
+  p->family = pair ? FAM_PAIR : FAM_SEQ;
+  // GBDCT_KERNEL_FAMILY=seq|pair|r64 forces a family when it supports the shape
+  // (used to test and compare every kernel family on the same inputs).
+  if (const char* f = getenv("GBDCT_KERNEL_FAMILY")) {
+    if (!strcmp(f, "seq")) p->family = FAM_SEQ;
+    else if (!strcmp(f, "pair") && pair) p->family = FAM_PAIR;
+    else if (!strcmp(f, "r64") && r64) p->family = FAM_R64;
+    else if (!strcmp(f, "fs") && fs) p->family = FAM_FS;
+  }
+  p->pmax = (p->family == FAM_R64 || p->family == FAM_FS) ? gbdct::r64::PMAX : 16;
+
   // Table layout, each block padded to 2 float2 (16 B).
-  const size_t t1 = round_up(gbdct::tw_size(n1) + 1, 2);
-  const size_t t2 = round_up(gbdct::tw_size(n2) + 1, 2);
+  const int tot1 = gbdct::tw_size_p(n1, p->pmax), tot2 = gbdct::tw_size_p(n2, p->pmax);
+  const size_t t1 = round_up(tot1 + 1, 2);
+  const size_t t2 = round_up(tot2 + 1, 2);
   const size_t ta = round_up(n1 / 2 + 1, 2);
   const size_t tb = round_up(n2, 2);
-  p->table_elems = t1 + t2 + 2 * ta + 2 * tb;
+  const size_t tf = (p->family == FAM_FS) ? round_up(n1, 2) : 0;
+  p->table_elems = t1 + t2 + 2 * ta + 2 * tb + tf;
   cudaError_t e = cudaMalloc(&p->tables, p->table_elems * sizeof(float2));
   if (e != cudaSuccess) {
     free_plan(p);
@@ -178,6 +220,7 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   float2* ia = fa + ta;
   float2* fb = ia + ta;
   float2* ib = fb + tb;
+  p->fstw = (p->family == FAM_FS) ? ib + tb : nullptr;
 
   p->work_bytes = (size_t)batch * (size_t)(n1 / 2) * (size_t)n2 * sizeof(float2);
   e = cudaMalloc(&p->work, p->work_bytes);
@@ -186,11 +229,14 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
     return cuda_status(e);
   }
 
-  const int tot1 = gbdct::tw_size(n1), tot2 = gbdct::tw_size(n2);
-  if (tot1 > 0) k_gen_stage_twiddles<<<(tot1 + 255) / 256, 256>>>(tw1, n1, tot1);
-  if (tot2 > 0) k_gen_stage_twiddles<<<(tot2 + 255) / 256, 256>>>(tw2, n2, tot2);
+  if (tot1 > 0) k_gen_stage_twiddles<<<(tot1 + 255) / 256, 256>>>(tw1, n1, p->pmax, tot1);
+  if (tot2 > 0) k_gen_stage_twiddles<<<(tot2 + 255) / 256, 256>>>(tw2, n2, p->pmax, tot2);
   const int nt = (n1 / 2 + 1 > n2) ? (n1 / 2 + 1) : n2;
   k_gen_dct_tables<<<(nt + 255) / 256, 256>>>(fa, fb, ia, ib, n1, n2);
+  if (p->fstw) {
+    const int A = (n1 == 1024) ? 32 : 64, B = n1 / A;
+    k_gen_fs_twiddles<<<(n1 + 255) / 256, 256>>>(p->fstw, n1, A, B);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -214,15 +260,29 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 
-  // Raise the dynamic shared-memory limit of the four kernels once.
-  Dct2dArgs ac = a, ar = a;
-  ac.seq_per_cta = p->b_cols;
-  ar.seq_per_cta = p->b_rows;
-  dim3 g(1, 1);
-  e = gbdct::run_fwd_cols(p->lg1, ac, g, 0, true);
-  if (e == cudaSuccess) e = gbdct::run_inv_cols(p->lg1, ac, g, 0, true);
-  if (e == cudaSuccess) e = gbdct::run_fwd_rows(p->lg2, ar, g, 0, true);
-  if (e == cudaSuccess) e = gbdct::run_inv_rows(p->lg2, ar, g, 0, true);
+  // Raise the dynamic shared-memory limit of the kernels once.
+  if (p->family == FAM_FS) {
+    e = gbdct::run_fs(p->lg1, p->lg2, false, a, p->fstw, 1, 0, true);
+  } else if (p->family == FAM_R64) {
+    e = gbdct::run_fwd_cols_r64(p->lg1, a, 1, 1, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_inv_cols_r64(p->lg1, a, 1, 1, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_fwd_rows_r64(p->lg2, a, 1, 1, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_inv_rows_r64(p->lg2, a, 1, 1, 0, true);
+  } else if (p->family == FAM_PAIR) {
+    e = gbdct::run_fwd_cols2(p->lg1, a, 1, 1, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_inv_cols2(p->lg1, a, 1, 1, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_fwd_rows2(p->lg2, a, 1, 1, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_inv_rows2(p->lg2, a, 1, 1, 0, true);
+  } else {
+    Dct2dArgs ac = a, ar = a;
+    ac.seq_per_cta = p->b_cols;
+    ar.seq_per_cta = p->b_rows;
+    dim3 g(1, 1);
+    e = gbdct::run_fwd_cols(p->lg1, ac, g, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_inv_cols(p->lg1, ac, g, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_fwd_rows(p->lg2, ar, g, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_inv_rows(p->lg2, ar, g, 0, true);
+  }
   if (e != cudaSuccess) {
     free_plan(p);
     return cuda_status(e);
@@ -245,12 +305,35 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
   a.in = static_cast<const float*>(in);
   a.out = static_cast<float*>(out);
   const int batch = (int)p->batch;
+  cudaError_t e;
+  if (p->family == FAM_FS) {
+    return cuda_status(gbdct::run_fs(p->lg1, p->lg2, inverse, a, p->fstw, batch, s, false));
+  }
+  if (p->family == FAM_R64) {
+    if (!inverse) {
+      e = gbdct::run_fwd_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
+      if (e == cudaSuccess) e = gbdct::run_fwd_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
+    } else {
+      e = gbdct::run_inv_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
+      if (e == cudaSuccess) e = gbdct::run_inv_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
+    }
+    return cuda_status(e);
+  }
+  if (p->family == FAM_PAIR) {
+    if (!inverse) {
+      e = gbdct::run_fwd_cols2(p->lg1, a, p->n2 / 4, batch, s, false);
+      if (e == cudaSuccess) e = gbdct::run_fwd_rows2(p->lg2, a, p->n1 / 4, batch, s, false);
+    } else {
+      e = gbdct::run_inv_rows2(p->lg2, a, p->n1 / 4, batch, s, false);
+      if (e == cudaSuccess) e = gbdct::run_inv_cols2(p->lg1, a, p->n2 / 4, batch, s, false);
+    }
+    return cuda_status(e);
+  }
   Dct2dArgs ac = a, ar = a;
   ac.seq_per_cta = p->b_cols;
   ar.seq_per_cta = p->b_rows;
   const dim3 gc((p->n2 / 2) / p->b_cols, batch);
   const dim3 gr((p->n1 / 2) / p->b_rows, batch);
-  cudaError_t e;
   if (!inverse) {
     e = gbdct::run_fwd_cols(p->lg1, ac, gc, s, false);
     if (e == cudaSuccess) e = gbdct::run_fwd_rows(p->lg2, ar, gr, s, false);
@@ -271,7 +354,15 @@ gbdct_status gbdct_exec_inverse(gbdct_plan_t plan, const void* in, void* out, vo
 
 size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_bytes : 0; }
 
-int gbdct_plan_launches_per_exec(gbdct_plan_t plan) { return plan ? 2 : 0; }
+int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
+  if (!plan) return 0;
+  return plan->family == FAM_FS ? 3 : 2;
+}
+
+const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
+  if (!plan) return "";
+  return plan->family == FAM_FS ? "fs" : plan->family == FAM_R64 ? "r64" : plan->family == FAM_PAIR ? "pair" : "seq";
+}
 
 gbdct_status gbdct_plan_destroy(gbdct_plan_t plan) {
   if (!plan) return GBDCT_OK;

@@ -141,3 +141,57 @@ def test_bad_pointers_are_rejected():
     assert plan.forward_ptr(base + 4, base) == binding.ERR_INVALID_ARG
     assert plan.inverse_ptr(base, base + 8) == binding.ERR_INVALID_ARG
     assert plan.forward_ptr(0, base) == binding.ERR_INVALID_ARG
+
+
+FAMILY_SUPPORT = {
+    "seq": lambda s: True,
+    "pair": lambda s: all(16 <= n <= 8192 for n in s),
+    "r64": lambda s: all(n in (4096, 8192) for n in s),
+    "fs": lambda s: s[0] in (1024, 2048, 4096) and s[1] in (4096, 8192),
+}
+
+
+@pytest.mark.parametrize("family", ["seq", "pair", "r64", "fs"])
+@pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192)])
+def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
+    """Each kernel family, forced through GBDCT_KERNEL_FAMILY, on the same inputs."""
+    if not FAMILY_SUPPORT[family](shape):
+        pytest.skip(f"{family} does not support {shape}")
+    monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
+    from paper_2110_01172_gb300 import Plan
+    plan = Plan(shape, "dct2")
+    assert plan.family == family
+    n1, n2 = shape
+    x = inputs.uniform(shape, seed=21)
+    xd = torch.from_numpy(x).cuda()
+    X = plan.forward(xd)
+    y = plan.inverse(X)
+    torch.cuda.synchronize()
+    Xh, yh = X.cpu().numpy(), y.cpu().numpy()
+    k1, k2 = _sample_indices(n1, n2, 40, seed=n1 * 7 + n2)
+    ref = oracle.dct2_2d_entries(x, k1, k2)
+    got = Xh[k1, k2].astype(np.float64)
+    assert np.abs(got - ref).max() <= MAX_ABS * np.abs(Xh).max()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= REL_L2
+    j1, j2 = _sample_indices(n1, n2, 16, seed=n1 + 3 * n2)
+    ref_inv = oracle.idct2_2d_entries(Xh, j1, j2)
+    assert np.abs(yh[j1, j2] - ref_inv).max() <= MAX_ABS * np.abs(yh).max()
+    check(yh, x.astype(np.float64))
+    plan.close()
+
+
+@pytest.mark.parametrize("family", ["seq", "pair"])
+@pytest.mark.parametrize("shape", [(256, 512), (64, 2048)])
+def test_small_families_full_oracle(family, shape, monkeypatch):
+    if not FAMILY_SUPPORT[family](shape):
+        pytest.skip(f"{family} does not support {shape}")
+    monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
+    from paper_2110_01172_gb300 import Plan
+    plan = Plan(shape, "dct2")
+    assert plan.family == family
+    x = inputs.uniform(shape, seed=5)
+    X = plan.forward(torch.from_numpy(x).cuda())
+    y = plan.inverse(X)
+    torch.cuda.synchronize()
+    check(X.cpu().numpy(), oracle.dct2_2d(x))
+    check(y.cpu().numpy(), oracle.idct2_2d(X.cpu().numpy()))
