@@ -124,6 +124,33 @@ const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
  * caller must make sure no stream still uses the plan. */
 gbdct_status gbdct_plan_destroy(gbdct_plan_t plan);
 
+/*
+ * Forward 2D DCT-II (same result as gbdct_exec_forward with a GBDCT_DCT2 plan)
+ * that allocates no device memory.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate on the call path - code
+ * running inside a host framework that owns all device memory through its own
+ * pool and forbids raw cudaMalloc, or latency-critical loops where a
+ * cudaMalloc/cudaFree (which may synchronise the whole device) would stall
+ * other streams.  Instead of a plan, the workspace and the twiddle tables live
+ * in one static device array of 5 MiB that every GPU which loads the library
+ * holds until the process exits; each call rebuilds the tables in it and then
+ * runs the two fused passes.
+ *   in, out  device pointers to n1*n2 float32 values, 16-byte aligned
+ *            (in == out allowed).
+ *   n1, n2   powers of two in [2, 16384] with n1*n2 <= 2^20 (1 Mi elements,
+ *            e.g. 1024 x 1024); larger sizes return GBDCT_ERR_UNSUPPORTED,
+ *            dims <= 0 return GBDCT_ERR_INVALID_ARG.
+ *   stream   cudaStream_t as void* (NULL = legacy default stream).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and sets kernel
+ * attributes; make that first call before any stream capture.  Calls issue no
+ * cudaMalloc, cudaFree or allocating library routine.  All calls on a device
+ * share the one array, which keeps the last call's contents: calls whose
+ * kernels overlap on the GPU (different streams, no ordering between them)
+ * race and give wrong results, so order them on one stream or with events.
+ */
+gbdct_status gbdct_dct2d_forward_noalloc(const void* in, void* out, int64_t n1, int64_t n2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_plan_launches_per_exec": (ctypes.c_int, [plan_p]),
             "gbdct_plan_kernel_family": (ctypes.c_char_p, [plan_p]),
             "gbdct_plan_destroy": (ctypes.c_int, [plan_p]),
+            "gbdct_dct2d_forward_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                           ctypes.c_int64, ctypes.c_void_p]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -222,3 +224,24 @@ def idct2(x, out=None):
     """Exact inverse of ``dct2`` (2/N-scaled DCT-III per axis)."""
     shape, batch = _split(x)
     return _cached_plan(shape, "dct2", batch, x.device).inverse(x, out)
+
+
+def dct2_noalloc(x, out=None, stream=None):
+    """2D DCT-II through the entry point that allocates no device memory.
+
+    For callers that cannot allocate on the call path (a host framework that
+    owns all device memory, or loops where a cudaMalloc would stall other
+    streams); the transform's scratch is a static device array shared by all
+    calls, so calls must not overlap on the GPU.  N1 * N2 <= 2**20.
+    """
+    torch = _torch()
+    lib = load()
+    if x.dim() != 2 or x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+        raise TypeError("expected a contiguous 2D CUDA float32 tensor")
+    if out is None:
+        out = torch.empty_like(x)
+    n1, n2 = x.shape
+    _check(lib.gbdct_dct2d_forward_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                           n1, n2, _stream_handle(stream, x.device)),
+           "gbdct_dct2d_forward_noalloc")
+    return out
