@@ -113,12 +113,20 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan);
 /* Number of kernel launches one exec call issues (0 for a NULL plan). */
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
 
-/* Name of the kernel family the plan runs ("seq", "pair" or "r64"; "" for a
+/* Name of the kernel family the plan runs ("seq", "pair", "r64", "fs" or "fsp"; "" for a
  * NULL plan).  Every family computes the same transform; the plan picks the
  * fastest one that supports the shape, and the environment variable
- * GBDCT_KERNEL_FAMILY=seq|pair|r64, read at plan creation, forces a family
+ * GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp, read at plan creation, forces a family
  * when it supports the shape (for testing and comparison). */
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
+
+/* Reports (and clears) a failure recorded on the device by the plan's
+ * kernels: the pipelined kernels bound every wait on an asynchronous copy, and
+ * a wait that gives up records it here instead of hanging the GPU (the
+ * transform's output is then invalid).  Synchronises with the device.
+ * Returns GBDCT_OK, GBDCT_ERR_TIMEOUT, GBDCT_ERR_INVALID_ARG (NULL plan) or
+ * GBDCT_ERR_CUDA. */
+gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan);
 
 /* Release the plan and its device memory.  NULL is accepted (no-op).  The
  * caller must make sure no stream still uses the plan. */

@@ -71,6 +71,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_plan_workspace_bytes": (ctypes.c_size_t, [plan_p]),
             "gbdct_plan_launches_per_exec": (ctypes.c_int, [plan_p]),
             "gbdct_plan_kernel_family": (ctypes.c_char_p, [plan_p]),
+            "gbdct_plan_check_device_error": (ctypes.c_int, [plan_p]),
             "gbdct_plan_destroy": (ctypes.c_int, [plan_p]),
             "gbdct_dct2d_forward_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                            ctypes.c_int64, ctypes.c_void_p]),
@@ -172,6 +173,10 @@ class Plan:
                                             ctypes.c_void_p(out.data_ptr()),
                                             _stream_handle(stream, x.device)), "gbdct_exec_inverse")
         return out
+
+    def check_device_error(self) -> int:
+        """Status of the device error word (OK, or ERR_TIMEOUT after a bounded wait gave up)."""
+        return int(self._lib.gbdct_plan_check_device_error(self._h))
 
     def forward_ptr(self, in_ptr: int, out_ptr: int, stream_ptr: int = 0) -> int:
         """Raw-pointer forward call (returns the status code, never raises)."""

@@ -53,6 +53,8 @@ struct Dct2dArgs {
   const float2* ia;   // conj(a_k1) / (N1 N2), k1 in [0, N1/2]
   const float2* ib;   // conj(b_k2), k2 in [0, N2)
   int seq_per_cta;    // B
+  const float2* fstw; // four-step twiddles W_N1^{n1a k1b} (four-step family only)
+  int* err;           // device error word: set to 1 by a bounded wait that gave up
 };
 
 template <int L>

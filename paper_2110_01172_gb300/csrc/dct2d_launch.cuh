@@ -69,6 +69,10 @@ cudaError_t launch_r64(void (*kern)(Dct2dArgs), const Dct2dArgs& a, int nitems, 
 cudaError_t run_fs(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, const float2* fstw, int batch,
                    cudaStream_t s, bool prepare);
 constexpr int kFsMinLog2N1 = 10, kFsMaxLog2N1 = 12, kFsMinLog2N2 = 12, kFsMaxLog2N2 = 13;
+// Persistent pipelined four-step family: N1 in {1024, 2048, 4096}, N2 = 4096;
+// `nsm` persistent CTAs at most.
+cudaError_t run_fsp(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int batch, int nsm, cudaStream_t s,
+                    bool prepare);
 
 constexpr int kPairMinLog2 = 4;
 constexpr int kPairMaxLog2 = 13;

@@ -107,6 +107,17 @@ __host__ __device__ constexpr float cos64(int k) {
   return t[((k % 64) + 64) % 64];
 }
 
+// Barrier used between stages: BAR == 0 is __syncthreads(); BAR > 0 is the
+// named barrier BAR over NT threads (a thread group inside a larger CTA).
+template <int BAR, int NT>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (BAR == 0) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+  }
+}
+
 template <int I, int N, typename F>
 __device__ __forceinline__ void static_for(F&& f) {
   if constexpr (I < N) {
@@ -232,7 +243,7 @@ __device__ __forceinline__ void first_stage(float2* v, float2* __restrict__ s, i
 // previous stage's stores).  Intermediate stages go through shared memory; the
 // last stage leaves its outputs in v: butterfly qb (< NB) of thread t holds
 // outputs (t + qb*TPS) + m * last_ns(L), m < R_last.
-template <int L, int NS, bool INV>
+template <int L, int NS, bool INV, int BAR = 0, int NT = 0>
 __device__ __forceinline__ void stages_to_regs(float2* __restrict__ s, int t, const float2* __restrict__ tw,
                                                float2* v) {
   constexpr int R = radix(L, NS);
@@ -246,7 +257,7 @@ __device__ __forceinline__ void stages_to_regs(float2* __restrict__ s, int t, co
     for (int j = 0; j < R; ++j) v[qb * R + j] = s[pidx(tb + j * STRIDE)];
   }
   if constexpr (NS * R < L) {
-    __syncthreads();
+    group_sync<BAR, NT>();
 #pragma unroll
     for (int qb = 0; qb < NB; ++qb) {
       const int tb = t + qb * TPS;
@@ -256,8 +267,8 @@ __device__ __forceinline__ void stages_to_regs(float2* __restrict__ s, int t, co
 #pragma unroll
       for (int m = 0; m < R; ++m) s[pidx(base + m * NS)] = v[qb * R + m];
     }
-    __syncthreads();
-    stages_to_regs<L, NS * R, INV>(s, t, tw, v);
+    group_sync<BAR, NT>();
+    stages_to_regs<L, NS * R, INV, BAR, NT>(s, t, tw, v);
   } else {
 #pragma unroll
     for (int qb = 0; qb < NB; ++qb) butterfly<L, NS, INV>(v + qb * R, t + qb * TPS, tw);

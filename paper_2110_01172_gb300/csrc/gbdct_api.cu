@@ -25,18 +25,21 @@ struct gbdct_plan_s {
   Dct2dArgs args;   // pointers and sizes shared by all passes
   int b_cols, b_rows;  // sequences per CTA of the column and row passes
   int family;          // kernel family: FAM_SEQ, FAM_PAIR, FAM_R64 or FAM_FS
-  float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS only)
+  float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS, FAM_FSP)
+  int* err;            // device error word (bounded waits that gave up)
+  int nsm;             // multiprocessors of the plan's device
   int pmax;            // points per thread of the stage structure (twiddle layout)
 };
 
 namespace {
 
 // Kernel families (all compute the same transform; chosen by size):
+//   FAM_FSP  FAM_FS as persistent TMA-bulk-copy pipelines, N1 in {1024..4096}, N2 = 4096
 //   FAM_FS   four-step column FFTs + radix-64 rows, N1 in {1024..4096}, N2 in {4096, 8192}
 //   FAM_R64  radix-64 register FFTs, N1 and N2 in {4096, 8192}
 //   FAM_PAIR two interleaved sequences per thread, 16 <= N1, N2 <= 8192
 //   FAM_SEQ  one sequence per thread group, any supported size
-enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_R64 = 2, FAM_FS = 3 };
+enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_R64 = 2, FAM_FS = 3, FAM_FSP = 4 };
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int64_t v) {
@@ -188,6 +191,7 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
                     p->lg2 >= gbdct::kPairMinLog2 && p->lg2 <= gbdct::kPairMaxLog2;
   const bool fs = p->lg1 >= gbdct::kFsMinLog2N1 && p->lg1 <= gbdct::kFsMaxLog2N1 &&
                   p->lg2 >= gbdct::kFsMinLog2N2 && p->lg2 <= gbdct::kFsMaxLog2N2;
+  const bool fsp = fs && p->lg2 == 12;
   // Default: the two-sequence family wherever it applies (fastest measured so
   // far); the radix-64 and four-step families are opt-in below.
   p->family = pair ? FAM_PAIR : FAM_SEQ;
@@ -198,8 +202,10 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
     else if (!strcmp(f, "pair") && pair) p->family = FAM_PAIR;
     else if (!strcmp(f, "r64") && r64) p->family = FAM_R64;
     else if (!strcmp(f, "fs") && fs) p->family = FAM_FS;
+    else if (!strcmp(f, "fsp") && fsp) p->family = FAM_FSP;
   }
-  p->pmax = (p->family == FAM_R64 || p->family == FAM_FS) ? gbdct::r64::PMAX : 16;
+  const bool four_step = p->family == FAM_FS || p->family == FAM_FSP;
+  p->pmax = (p->family == FAM_R64 || four_step) ? gbdct::r64::PMAX : 16;
 
   // Table layout, each block padded to 2 float2 (16 B).
   const int tot1 = gbdct::tw_size_p(n1, p->pmax), tot2 = gbdct::tw_size_p(n2, p->pmax);
@@ -207,8 +213,8 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   const size_t t2 = round_up(tot2 + 1, 2);
   const size_t ta = round_up(n1 / 2 + 1, 2);
   const size_t tb = round_up(n2, 2);
-  const size_t tf = (p->family == FAM_FS) ? round_up(n1, 2) : 0;
-  p->table_elems = t1 + t2 + 2 * ta + 2 * tb + tf;
+  const size_t tf = four_step ? round_up(n1, 2) : 0;
+  p->table_elems = t1 + t2 + 2 * ta + 2 * tb + tf + 2;  // + 16 bytes for the error word
   cudaError_t e = cudaMalloc(&p->tables, p->table_elems * sizeof(float2));
   if (e != cudaSuccess) {
     free_plan(p);
@@ -220,7 +226,8 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   float2* ia = fa + ta;
   float2* fb = ia + ta;
   float2* ib = fb + tb;
-  p->fstw = (p->family == FAM_FS) ? ib + tb : nullptr;
+  p->fstw = four_step ? ib + tb : nullptr;
+  p->err = reinterpret_cast<int*>(ib + tb + tf);
 
   p->work_bytes = (size_t)batch * (size_t)(n1 / 2) * (size_t)n2 * sizeof(float2);
   e = cudaMalloc(&p->work, p->work_bytes);
@@ -238,6 +245,8 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
     k_gen_fs_twiddles<<<(n1 + 255) / 256, 256>>>(p->fstw, n1, A, B);
   }
   e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemset(p->err, 0, 16);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_plan(p);
@@ -257,11 +266,15 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   a.fb = fb;
   a.ia = ia;
   a.ib = ib;
+  a.fstw = p->fstw;
+  a.err = p->err;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 
   // Raise the dynamic shared-memory limit of the kernels once.
-  if (p->family == FAM_FS) {
+  if (p->family == FAM_FSP) {
+    e = gbdct::run_fsp(p->lg1, p->lg2, false, a, 1, p->nsm, 0, true);
+  } else if (p->family == FAM_FS) {
     e = gbdct::run_fs(p->lg1, p->lg2, false, a, p->fstw, 1, 0, true);
   } else if (p->family == FAM_R64) {
     e = gbdct::run_fwd_cols_r64(p->lg1, a, 1, 1, 0, true);
@@ -306,6 +319,9 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
   a.out = static_cast<float*>(out);
   const int batch = (int)p->batch;
   cudaError_t e;
+  if (p->family == FAM_FSP) {
+    return cuda_status(gbdct::run_fsp(p->lg1, p->lg2, inverse, a, batch, p->nsm, s, false));
+  }
   if (p->family == FAM_FS) {
     return cuda_status(gbdct::run_fs(p->lg1, p->lg2, inverse, a, p->fstw, batch, s, false));
   }
@@ -356,12 +372,23 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_
 
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (!plan) return 0;
-  return plan->family == FAM_FS ? 3 : 2;
+  return (plan->family == FAM_FS || plan->family == FAM_FSP) ? 3 : 2;
 }
 
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
   if (!plan) return "";
-  return plan->family == FAM_FS ? "fs" : plan->family == FAM_R64 ? "r64" : plan->family == FAM_PAIR ? "pair" : "seq";
+  return plan->family == FAM_FSP ? "fsp" : plan->family == FAM_FS ? "fs" : plan->family == FAM_R64 ? "r64" : plan->family == FAM_PAIR ? "pair" : "seq";
+}
+
+gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan) {
+  if (!plan) return GBDCT_ERR_INVALID_ARG;
+  DeviceGuard guard(plan->device);
+  int v = 0;
+  if (cudaMemcpy(&v, plan->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBDCT_ERR_CUDA;
+  if (v == 0) return GBDCT_OK;
+  const int zero = 0;
+  cudaMemcpy(plan->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  return GBDCT_ERR_TIMEOUT;
 }
 
 gbdct_status gbdct_plan_destroy(gbdct_plan_t plan) {

@@ -148,11 +148,12 @@ FAMILY_SUPPORT = {
     "pair": lambda s: all(16 <= n <= 8192 for n in s),
     "r64": lambda s: all(n in (4096, 8192) for n in s),
     "fs": lambda s: s[0] in (1024, 2048, 4096) and s[1] in (4096, 8192),
+    "fsp": lambda s: s[0] in (1024, 2048, 4096) and s[1] == 4096,
 }
 
 
-@pytest.mark.parametrize("family", ["seq", "pair", "r64", "fs"])
-@pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192)])
+@pytest.mark.parametrize("family", ["seq", "pair", "r64", "fs", "fsp"])
+@pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192), (1024, 4096)])
 def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
     """Each kernel family, forced through GBDCT_KERNEL_FAMILY, on the same inputs."""
     if not FAMILY_SUPPORT[family](shape):
@@ -177,7 +178,28 @@ def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
     ref_inv = oracle.idct2_2d_entries(Xh, j1, j2)
     assert np.abs(yh[j1, j2] - ref_inv).max() <= MAX_ABS * np.abs(yh).max()
     check(yh, x.astype(np.float64))
+    from paper_2110_01172_gb300 import binding
+    assert plan.check_device_error() == binding.OK
     plan.close()
+
+
+def test_batched_pipelined_family(monkeypatch):
+    monkeypatch.setenv("GBDCT_KERNEL_FAMILY", "fsp")
+    from paper_2110_01172_gb300 import Plan, binding
+    shape = (1024, 4096)
+    plan = Plan(shape, "dct2", batch=2)
+    assert plan.family == "fsp"
+    xs = np.stack([inputs.uniform(shape, seed=s) for s in (31, 32)])
+    X = plan.forward(torch.from_numpy(xs).cuda())
+    y = plan.inverse(X)
+    torch.cuda.synchronize()
+    Xh, yh = X.cpu().numpy(), y.cpu().numpy()
+    for b in range(2):
+        k1, k2 = _sample_indices(*shape, 24, seed=b)
+        ref = oracle.dct2_2d_entries(xs[b], k1, k2)
+        assert np.abs(Xh[b][k1, k2] - ref).max() <= MAX_ABS * np.abs(Xh[b]).max()
+        check(yh[b], xs[b].astype(np.float64))
+    assert plan.check_device_error() == binding.OK
 
 
 @pytest.mark.parametrize("family", ["seq", "pair"])
