@@ -54,10 +54,12 @@ typedef enum gbdct_kind {
      DST-II(x)_k = DCT-II((-1)^n x)_{N-1-k} on each axis. */
   GBDCT_DST2 = 1,
   /* inverse: IDCT on axis 0 and IDXST on axis 1 (Section V-B, Eq. idxst,
-     "IDCT_IDXST"); forward: the exact inverse of that map. */
+     "IDCT_IDXST"), with the same 2/N scaling as the DCT-II inverse.  IDXST
+     ignores x_0, so the map is singular: exec_forward returns
+     GBDCT_ERR_UNSUPPORTED for this kind. */
   GBDCT_IDCT_IDXST = 2,
-  /* inverse: IDXST on axis 0 and IDCT on axis 1 ("IDXST_IDCT"); forward: its
-     exact inverse. */
+  /* inverse: IDXST on axis 0 and IDCT on axis 1 ("IDXST_IDCT"); inverse only,
+     like GBDCT_IDCT_IDXST. */
   GBDCT_IDXST_IDCT = 3
 } gbdct_kind;
 
@@ -81,7 +83,9 @@ const char* gbdct_version(void);
  *   ndim  2 (3 returns GBDCT_ERR_UNSUPPORTED in this build).
  *   dims  ndim sizes; each must be a power of two between 2 and 16384, else
  *         GBDCT_ERR_UNSUPPORTED (dims <= 0 give GBDCT_ERR_INVALID_ARG).
- *   kind  a gbdct_kind; dtype must be GBDCT_F32.
+ *   kind  a gbdct_kind; dtype must be GBDCT_F32.  Kinds other than
+ *         GBDCT_DCT2 run the DCT-II kernels between two index/sign map kernels
+ *         and own an extra staging array of batch*N1*N2 floats.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises the device.
  */
 gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims,
@@ -131,6 +135,35 @@ gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan);
 /* Release the plan and its device memory.  NULL is accepted (no-op).  The
  * caller must make sure no stream still uses the plan. */
 gbdct_status gbdct_plan_destroy(gbdct_plan_t plan);
+
+/*
+ * Spectral Neumann Poisson solve of Section V-B, Algorithm 4 (the electrostatic
+ * step of analytical placement).  For a density map rho (N1 x N2 float32):
+ *   a    = DCT-II(rho)                                   (forward, as above)
+ *   psi  = IDCT2(a / (wu^2 + wv^2))                      potential
+ *   xi0  = IDXST_IDCT(a wu / (wu^2 + wv^2))              field along axis 0
+ *   xi1  = IDCT_IDXST(a wv / (wu^2 + wv^2))              field along axis 1
+ * with wu = pi u / N1, wv = pi v / N2 and the (0,0) term set to zero (the paper
+ * only says "scaled a1, a2"; these are the eigenfrequencies of the cosine
+ * basis in grid units).  The solver owns three plans (DCT2, IDXST_IDCT,
+ * IDCT_IDXST) and the w tables (FP64-generated, stored FP32).
+ */
+typedef struct gbdct_poisson_s* gbdct_poisson_t;
+
+/* Shape limits as gbdct_plan_create (powers of two, 2..16384). */
+gbdct_status gbdct_poisson_create(gbdct_poisson_t* out, int64_t n1, int64_t n2);
+
+/* rho, psi, xi0, xi1: device float32 arrays of N1*N2, 16-byte aligned; psi, xi0
+ * and xi1 must be distinct (rho may alias psi).  Asynchronous on `stream`; a
+ * solver may be used by one stream at a time. */
+gbdct_status gbdct_poisson_solve(gbdct_poisson_t p, const void* rho, void* psi, void* xi0, void* xi1,
+                                 void* stream);
+
+/* Device bytes owned by the solver (workspaces, staging and tables). */
+size_t gbdct_poisson_workspace_bytes(gbdct_poisson_t p);
+
+/* Releases the solver (NULL accepted). */
+gbdct_status gbdct_poisson_destroy(gbdct_poisson_t p);
 
 /*
  * Forward 2D DCT-II (same result as gbdct_exec_forward with a GBDCT_DCT2 plan)

@@ -73,6 +73,11 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_plan_kernel_family": (ctypes.c_char_p, [plan_p]),
             "gbdct_plan_check_device_error": (ctypes.c_int, [plan_p]),
             "gbdct_plan_destroy": (ctypes.c_int, [plan_p]),
+            "gbdct_poisson_create": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int64, ctypes.c_int64]),
+            "gbdct_poisson_solve": (ctypes.c_int, [plan_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p]),
+            "gbdct_poisson_workspace_bytes": (ctypes.c_size_t, [plan_p]),
+            "gbdct_poisson_destroy": (ctypes.c_int, [plan_p]),
             "gbdct_dct2d_forward_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                            ctypes.c_int64, ctypes.c_void_p]),
         }
@@ -199,6 +204,51 @@ class Plan:
             pass
 
 
+class PoissonSolver:
+    """Spectral Neumann Poisson solver (Algorithm 4): rho -> (psi, xi0, xi1) on one GPU."""
+
+    def __init__(self, shape, device=None):
+        torch = _torch()
+        lib = load()
+        self.shape = tuple(int(s) for s in shape)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.gbdct_poisson_create(ctypes.byref(h), *self.shape), "gbdct_poisson_create")
+        self._h = h
+        self._lib = lib
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.gbdct_poisson_workspace_bytes(self._h))
+
+    def solve(self, rho, psi=None, xi0=None, xi1=None, stream=None):
+        torch = _torch()
+        if rho.dtype != torch.float32 or not rho.is_cuda or tuple(rho.shape) != self.shape:
+            raise ValueError(f"expected a CUDA float32 tensor of shape {self.shape}")
+        rho = rho.contiguous()
+        psi = torch.empty_like(rho) if psi is None else psi
+        xi0 = torch.empty_like(rho) if xi0 is None else xi0
+        xi1 = torch.empty_like(rho) if xi1 is None else xi1
+        _check(self._lib.gbdct_poisson_solve(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                             ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(xi0.data_ptr()),
+                                             ctypes.c_void_p(xi1.data_ptr()), _stream_handle(stream, rho.device)),
+               "gbdct_poisson_solve")
+        return psi, xi0, xi1
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gbdct_poisson_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 _plans: dict = {}
 
 
@@ -229,6 +279,30 @@ def idct2(x, out=None):
     """Exact inverse of ``dct2`` (2/N-scaled DCT-III per axis)."""
     shape, batch = _split(x)
     return _cached_plan(shape, "dct2", batch, x.device).inverse(x, out)
+
+
+def dst2(x, out=None):
+    """2D DST-II (unnormalised sine analogue of ``dct2``)."""
+    shape, batch = _split(x)
+    return _cached_plan(shape, "dst2", batch, x.device).forward(x, out)
+
+
+def idst2(x, out=None):
+    """Exact inverse of ``dst2``."""
+    shape, batch = _split(x)
+    return _cached_plan(shape, "dst2", batch, x.device).inverse(x, out)
+
+
+def idct_idxst(x, out=None):
+    """IDCT along axis 0 and IDXST along axis 1 (2/N-scaled, like ``idct2``)."""
+    shape, batch = _split(x)
+    return _cached_plan(shape, "idct_idxst", batch, x.device).inverse(x, out)
+
+
+def idxst_idct(x, out=None):
+    """IDXST along axis 0 and IDCT along axis 1."""
+    shape, batch = _split(x)
+    return _cached_plan(shape, "idxst_idct", batch, x.device).inverse(x, out)
 
 
 def dct2_noalloc(x, out=None, stream=None):

@@ -28,6 +28,7 @@ struct gbdct_plan_s {
   float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS, FAM_FSP)
   int* err;            // device error word (bounded waits that gave up)
   int nsm;             // multiprocessors of the plan's device
+  float* tmp;          // variant kinds: staging array (batch * N1 * N2 floats)
   int pmax;            // points per thread of the stage structure (twiddle layout)
 };
 
@@ -105,6 +106,28 @@ __global__ void k_gen_fs_twiddles(float2* out, int n1, int A, int B) {
   out[idx] = make_float2((float)cs, (float)sn);
 }
 
+// Index map used by the DST-II and IDXST kinds around the DCT-II core:
+// out(i, j) = sign(i, j) * in(src(i), src(j)) where, per axis, src(i) is i,
+// N-1-i (reversal) or N-i with src(0) -> 0 value (the IDXST shift x_{N-n},
+// x_N = 0, Section V-B Eq. idxst), and sign is (-1)^i on the flagged axes.
+struct MapSpec {
+  int rev0, rev1, shift0, shift1, sgn0, sgn1;
+};
+
+__global__ void k_map2d(const float* __restrict__ in, float* __restrict__ out, int n1, int n2, long long bs,
+                        MapSpec m) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= n2) return;
+  const float* src = in + (long long)blockIdx.z * bs;
+  float* dst = out + (long long)blockIdx.z * bs;
+  const int si = m.rev0 ? n1 - 1 - i : (m.shift0 ? (i ? n1 - i : -1) : i);
+  const int sj = m.rev1 ? n2 - 1 - j : (m.shift1 ? (j ? n2 - j : -1) : j);
+  float v = (si < 0 || sj < 0) ? 0.f : src[(long long)si * n2 + sj];
+  if (((m.sgn0 & i) ^ (m.sgn1 & j)) & 1) v = -v;
+  dst[(long long)i * n2 + j] = v;
+}
+
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 gbdct_status cuda_status(cudaError_t e) {
@@ -131,6 +154,7 @@ void free_plan(gbdct_plan_s* p) {
   if (!p) return;
   if (p->tables) cudaFree(p->tables);
   if (p->work) cudaFree(p->work);
+  if (p->tmp) cudaFree(p->tmp);
   delete p;
 }
 
@@ -161,7 +185,6 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
   if (dtype != GBDCT_F32) return GBDCT_ERR_UNSUPPORTED;
   if (ndim != 2) return GBDCT_ERR_UNSUPPORTED;
-  if (kind != GBDCT_DCT2) return GBDCT_ERR_UNSUPPORTED;
   for (int i = 0; i < ndim; ++i) {
     if (!is_pow2(dims[i])) return GBDCT_ERR_UNSUPPORTED;
     const int lg = ilog2(dims[i]);
@@ -231,6 +254,8 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
 
   p->work_bytes = (size_t)batch * (size_t)(n1 / 2) * (size_t)n2 * sizeof(float2);
   e = cudaMalloc(&p->work, p->work_bytes);
+  if (e == cudaSuccess && kind != GBDCT_DCT2)
+    e = cudaMalloc(&p->tmp, (size_t)batch * (size_t)n1 * (size_t)n2 * sizeof(float));
   if (e != cudaSuccess) {
     free_plan(p);
     return cuda_status(e);
@@ -309,11 +334,52 @@ gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims,
   return gbdct_plan_create_batched(out, ndim, dims, 1, kind, dtype);
 }
 
+static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse);
+
+static cudaError_t run_map(gbdct_plan_t p, const float* in, float* out, MapSpec m, cudaStream_t s) {
+  const dim3 grid((p->n2 + 255) / 256, p->n1, (unsigned)p->batch);
+  k_map2d<<<grid, 256, 0, s>>>(in, out, p->n1, p->n2, (long long)p->n1 * p->n2, m);
+  return cudaGetLastError();
+}
+
+// DST-II and the IDXST kinds as index/sign maps around the DCT-II core:
+//   DST-II(x)_k = DCT-II((-1)^n x)_{N-1-k} per axis (both axes);
+//   IDXST(x)_k = (-1)^k IDCT({x_{N-n}})_k, x_N = 0 (Section V-B, Eq. idxst).
 static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stream, bool inverse) {
   if (!p || !in || !out) return GBDCT_ERR_INVALID_ARG;
   if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return GBDCT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse);
+  MapSpec pre{}, post{};
+  if (p->kind == GBDCT_DST2) {
+    if (!inverse) {
+      pre.sgn0 = pre.sgn1 = 1;
+      post.rev0 = post.rev1 = 1;
+    } else {
+      pre.rev0 = pre.rev1 = 1;
+      post.sgn0 = post.sgn1 = 1;
+    }
+  } else {
+    // IDXST ignores x_0, so the IDCT_IDXST / IDXST_IDCT maps are singular and
+    // have no forward (inverse-of-inverse) transform.
+    if (!inverse) return GBDCT_ERR_UNSUPPORTED;
+    if (p->kind == GBDCT_IDCT_IDXST) {
+      pre.shift1 = 1;
+      post.sgn1 = 1;
+    } else {
+      pre.shift0 = 1;
+      post.sgn0 = 1;
+    }
+  }
+  cudaError_t e = run_map(p, static_cast<const float*>(in), p->tmp, pre, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  const gbdct_status st = exec_core(p, p->tmp, p->tmp, s, inverse);
+  if (st != GBDCT_OK) return st;
+  return cuda_status(run_map(p, p->tmp, static_cast<float*>(out), post, s));
+}
+
+static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse) {
   Dct2dArgs a = p->args;
   a.in = static_cast<const float*>(in);
   a.out = static_cast<float*>(out);
@@ -372,7 +438,8 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_
 
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (!plan) return 0;
-  return (plan->family == FAM_FS || plan->family == FAM_FSP) ? 3 : 2;
+  const int core = (plan->family == FAM_FS || plan->family == FAM_FSP) ? 3 : 2;
+  return plan->kind == GBDCT_DCT2 ? core : core + 2;
 }
 
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
