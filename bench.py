@@ -48,7 +48,15 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
 # from the ncu capture summarised in profiles/, valid only for the kernel
 # sources with this digest (otherwise reported as null).
-TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+TRAFFIC = {
+    "sources_sha256": "1f9e4d7a440fa9d4eaef81d83202c488b30bf57f5d05a43de4897d18cdd53cf4",
+    "bytes_per_launch": {   # profiles/pair_kernels_4096_ncu.md (cold L2 under ncu)
+        "forward column pass (reorder + column FFT + split)": 67285504 + 19485184,
+        "forward row pass (row FFT + symmetric-pair postprocess)": 67225088 + 18865664,
+        "inverse row pass (four-read preprocess + row IFFT)": 67237632 + 20116480,
+        "inverse column pass (column IFFT + inverse reorder)": 70111232 + 21584128,
+    },
+}
 
 
 def parse_args(argv=None):
@@ -61,6 +69,8 @@ def parse_args(argv=None):
     ap.add_argument("--n2", type=int, default=N2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300)
     return ap.parse_args(argv)
 
 
@@ -257,6 +267,31 @@ def run_reference(args):
     return 0
 
 
+SERVE_RATES = (2000.0, 5000.0, 10000.0, 20000.0)
+
+
+def run_serving(args, dev):
+    """Poisson-arrival spectral Poisson solves: continuous batching vs one at a time."""
+    import torch
+    from paper_2110_01172_gb300.serving import (PoissonServer, _Resources, latency_summary, make_requests,
+                                                serve_plain)
+    n = args.serve_requests
+    sets = {rate: make_requests(n, rate, seed=int(rate)) for rate in SERVE_RATES}
+    shapes = sorted({tuple(r.rho.shape) for reqs in sets.values() for r in reqs})
+    server = PoissonServer(slots=8, device=dev.index)
+    server.warm(shapes, per_shape=2)
+    server.serve(make_requests(64, 1e6, seed=1))   # first use of every code path
+    solvers = {sh: _Resources(sh, dev) for sh in shapes}
+    out = {"requests_per_rate": n, "slots": 8, "sizes": "N1, N2 in {64, ..., 2048}, 100-2000 blobs",
+           "rates": []}
+    for rate, reqs in sets.items():
+        served = latency_summary(server.serve(reqs))
+        plain = latency_summary(serve_plain(reqs, device=dev.index, solvers=solvers))
+        out["rates"].append({"rate_per_s": rate, "served": served, "plain": plain})
+    torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_init("nccl")
@@ -336,13 +371,34 @@ def run_ours(args):
     if not err < 1e-4:
         raise RuntimeError(f"end-to-end reconstruction error {err}")
 
+    # per-kernel durations: each launch of the two sequences timed alone on the
+    # launching stream (same buffers as the full calls)
+    kernels = []
+    for inverse in (False, True):
+        for k in range(plan.launches_per_exec):
+            src = cs if inverse else xs
+            dst = ys if inverse else cs
+            us = time_loop(lambda i, k=k, inverse=inverse, src=src, dst=dst:
+                           plan.step(inverse, k, src[i % NBUF], dst[i % NBUF]), iters)
+            kernels.append({"name": ("inverse " if inverse else "forward ") + plan.step_name(inverse, k),
+                            "us": us})
+    # restore valid spectra/outputs after the single-step runs
+    for i in range(NBUF):
+        step(i)
+    torch.cuda.synchronize()
+
     peak, peak_kind = measured_peaks()
-    algo_bytes = 8.0 * n1 * n2          # one read + one write of the float32 array
-    dom_us = max(fwd_us, inv_us)
-    dom_name = "inverse" if inv_us >= fwd_us else "forward"
-    achieved = algo_bytes / (dom_us * 1e-6) / 1e9
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha256"] == sources_digest() else None
+    algo_bytes = 8.0 * n1 * n2          # one read + one write of an N1 x N2 float32 array
+    dom = max(kernels, key=lambda k: k["us"])
+    achieved = algo_bytes / (dom["us"] * 1e-6) / 1e9
+    traffic = None
+    if TRAFFIC["sources_sha256"] == sources_digest() and plan.family == "pair" and (n1, n2) == (4096, 4096):
+        traffic = TRAFFIC["bytes_per_launch"].get(dom["name"])
     launches = plan.launches_per_exec
+
+    serve = None
+    if not args.no_serve:
+        serve = run_serving(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -363,11 +419,19 @@ def run_ours(args):
             "transforms_per_s": sum_over_ranks(2e6 / step_us, world, dev) if world > 1 else 2e6 / step_us,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"{dom_name} transform ({launches} launches)",
+                         "kernel": dom["name"], "kernel_us": dom["us"],
+                         "algorithmic_bytes_per_launch": algo_bytes,
                          "peak_source": f"{peak_kind} hbm_gbs"},
+            "transform_roofline": {"dct_frac": algo_bytes / (fwd_us * 1e-6) / 1e9 / peak,
+                                   "idct_frac": algo_bytes / (inv_us * 1e-6) / 1e9 / peak},
+            "kernels": kernels,
+            "kernel_family": plan.family,
+            "serve": serve,
             "e2e": {"value": e2e_us, "unit": UNIT, "h2d_bytes_per_step": 4 * n1 * n2,
                     "d2h_bytes_per_step": 4 * n1 * n2},
             "gpu_launches": args.steps * 2 * launches,
+            "serve_p50_ms": serve["rates"][1]["served"]["p50_ms"] if serve else None,
+            "serve_p99_ms": serve["rates"][1]["served"]["p99_ms"] if serve else None,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -111,6 +111,19 @@ gbdct_status gbdct_exec_forward(gbdct_plan_t plan, const void* in, void* out, vo
 /* Inverse transform; same contract as gbdct_exec_forward. */
 gbdct_status gbdct_exec_inverse(gbdct_plan_t plan, const void* in, void* out, void* stream);
 
+/*
+ * Diagnostic: runs launch `step` (0 <= step < gbdct_plan_launches_per_exec) of
+ * the forward (inverse = 0) or inverse (inverse = 1) sequence alone, reading
+ * and writing the same buffers the full call would.  Used to time each kernel
+ * of a transform on its own stream; the result of a single step is an
+ * intermediate, not a transform.  Errors: INVALID_ARG (NULL plan, step out of
+ * range, NULL/misaligned pointers), UNSUPPORTED, CUDA.
+ */
+gbdct_status gbdct_exec_step(gbdct_plan_t plan, int inverse, int step, const void* in, void* out, void* stream);
+
+/* Short description of launch `step` (static storage; "" when out of range). */
+const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step);
+
 /* Bytes of device workspace owned by the plan (0 for a NULL plan). */
 size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan);
 

@@ -72,6 +72,9 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_plan_launches_per_exec": (ctypes.c_int, [plan_p]),
             "gbdct_plan_kernel_family": (ctypes.c_char_p, [plan_p]),
             "gbdct_plan_check_device_error": (ctypes.c_int, [plan_p]),
+            "gbdct_exec_step": (ctypes.c_int, [plan_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
+            "gbdct_plan_step_name": (ctypes.c_char_p, [plan_p, ctypes.c_int, ctypes.c_int]),
             "gbdct_plan_destroy": (ctypes.c_int, [plan_p]),
             "gbdct_poisson_create": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int64, ctypes.c_int64]),
             "gbdct_poisson_solve": (ctypes.c_int, [plan_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -178,6 +181,16 @@ class Plan:
                                             ctypes.c_void_p(out.data_ptr()),
                                             _stream_handle(stream, x.device)), "gbdct_exec_inverse")
         return out
+
+    def step(self, inverse: bool, step: int, x, out, stream=None):
+        """Run launch `step` of the forward/inverse sequence alone (per-kernel timing)."""
+        _check(self._lib.gbdct_exec_step(self._h, int(bool(inverse)), int(step), ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, x.device)),
+               "gbdct_exec_step")
+        return out
+
+    def step_name(self, inverse: bool, step: int) -> str:
+        return self._lib.gbdct_plan_step_name(self._h, int(bool(inverse)), int(step)).decode()
 
     def check_device_error(self) -> int:
         """Status of the device error word (OK, or ERR_TIMEOUT after a bounded wait gave up)."""

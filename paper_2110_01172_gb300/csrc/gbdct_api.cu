@@ -293,6 +293,7 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   a.ib = ib;
   a.fstw = p->fstw;
   a.err = p->err;
+  a.step_filter = -1;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 
@@ -334,7 +335,9 @@ gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims,
   return gbdct_plan_create_batched(out, ndim, dims, 1, kind, dtype);
 }
 
-static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse);
+static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse,
+                              int step = -1);
+static int core_launches(gbdct_plan_t p) { return (p->family == FAM_FS || p->family == FAM_FSP) ? 3 : 2; }
 
 static cudaError_t run_map(gbdct_plan_t p, const float* in, float* out, MapSpec m, cudaStream_t s) {
   const dim3 grid((p->n2 + 255) / 256, p->n1, (unsigned)p->batch);
@@ -345,12 +348,13 @@ static cudaError_t run_map(gbdct_plan_t p, const float* in, float* out, MapSpec 
 // DST-II and the IDXST kinds as index/sign maps around the DCT-II core:
 //   DST-II(x)_k = DCT-II((-1)^n x)_{N-1-k} per axis (both axes);
 //   IDXST(x)_k = (-1)^k IDCT({x_{N-n}})_k, x_N = 0 (Section V-B, Eq. idxst).
-static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stream, bool inverse) {
+static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stream, bool inverse,
+                           int step = -1) {
   if (!p || !in || !out) return GBDCT_ERR_INVALID_ARG;
   if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return GBDCT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse);
+  if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse, step);
   MapSpec pre{}, post{};
   if (p->kind == GBDCT_DST2) {
     if (!inverse) {
@@ -372,19 +376,28 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
       post.sgn0 = 1;
     }
   }
-  cudaError_t e = run_map(p, static_cast<const float*>(in), p->tmp, pre, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  const gbdct_status st = exec_core(p, p->tmp, p->tmp, s, inverse);
-  if (st != GBDCT_OK) return st;
-  return cuda_status(run_map(p, p->tmp, static_cast<float*>(out), post, s));
+  const int nc = core_launches(p);
+  if (step < 0 || step == 0) {
+    const cudaError_t e = run_map(p, static_cast<const float*>(in), p->tmp, pre, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (step < 0 || (step >= 1 && step <= nc)) {
+    const gbdct_status st = exec_core(p, p->tmp, p->tmp, s, inverse, step < 0 ? -1 : step - 1);
+    if (st != GBDCT_OK) return st;
+  }
+  if (step < 0 || step == nc + 1) return cuda_status(run_map(p, p->tmp, static_cast<float*>(out), post, s));
+  return GBDCT_OK;
 }
 
-static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse) {
+static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse,
+                              int step) {
   Dct2dArgs a = p->args;
   a.in = static_cast<const float*>(in);
   a.out = static_cast<float*>(out);
+  a.step_filter = step;
   const int batch = (int)p->batch;
-  cudaError_t e;
+  const bool s0 = step < 0 || step == 0, s1 = step < 0 || step == 1;
+  cudaError_t e = cudaSuccess;
   if (p->family == FAM_FSP) {
     return cuda_status(gbdct::run_fsp(p->lg1, p->lg2, inverse, a, batch, p->nsm, s, false));
   }
@@ -393,21 +406,21 @@ static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStr
   }
   if (p->family == FAM_R64) {
     if (!inverse) {
-      e = gbdct::run_fwd_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
-      if (e == cudaSuccess) e = gbdct::run_fwd_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
+      if (s0) e = gbdct::run_fwd_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
+      if (e == cudaSuccess && s1) e = gbdct::run_fwd_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
     } else {
-      e = gbdct::run_inv_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
-      if (e == cudaSuccess) e = gbdct::run_inv_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
+      if (s0) e = gbdct::run_inv_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
+      if (e == cudaSuccess && s1) e = gbdct::run_inv_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
     }
     return cuda_status(e);
   }
   if (p->family == FAM_PAIR) {
     if (!inverse) {
-      e = gbdct::run_fwd_cols2(p->lg1, a, p->n2 / 4, batch, s, false);
-      if (e == cudaSuccess) e = gbdct::run_fwd_rows2(p->lg2, a, p->n1 / 4, batch, s, false);
+      if (s0) e = gbdct::run_fwd_cols2(p->lg1, a, p->n2 / 4, batch, s, false);
+      if (e == cudaSuccess && s1) e = gbdct::run_fwd_rows2(p->lg2, a, p->n1 / 4, batch, s, false);
     } else {
-      e = gbdct::run_inv_rows2(p->lg2, a, p->n1 / 4, batch, s, false);
-      if (e == cudaSuccess) e = gbdct::run_inv_cols2(p->lg1, a, p->n2 / 4, batch, s, false);
+      if (s0) e = gbdct::run_inv_rows2(p->lg2, a, p->n1 / 4, batch, s, false);
+      if (e == cudaSuccess && s1) e = gbdct::run_inv_cols2(p->lg1, a, p->n2 / 4, batch, s, false);
     }
     return cuda_status(e);
   }
@@ -417,11 +430,11 @@ static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStr
   const dim3 gc((p->n2 / 2) / p->b_cols, batch);
   const dim3 gr((p->n1 / 2) / p->b_rows, batch);
   if (!inverse) {
-    e = gbdct::run_fwd_cols(p->lg1, ac, gc, s, false);
-    if (e == cudaSuccess) e = gbdct::run_fwd_rows(p->lg2, ar, gr, s, false);
+    if (s0) e = gbdct::run_fwd_cols(p->lg1, ac, gc, s, false);
+    if (e == cudaSuccess && s1) e = gbdct::run_fwd_rows(p->lg2, ar, gr, s, false);
   } else {
-    e = gbdct::run_inv_rows(p->lg2, ar, gr, s, false);
-    if (e == cudaSuccess) e = gbdct::run_inv_cols(p->lg1, ac, gc, s, false);
+    if (s0) e = gbdct::run_inv_rows(p->lg2, ar, gr, s, false);
+    if (e == cudaSuccess && s1) e = gbdct::run_inv_cols(p->lg1, ac, gc, s, false);
   }
   return cuda_status(e);
 }
@@ -432,6 +445,32 @@ gbdct_status gbdct_exec_forward(gbdct_plan_t plan, const void* in, void* out, vo
 
 gbdct_status gbdct_exec_inverse(gbdct_plan_t plan, const void* in, void* out, void* stream) {
   return exec2d(plan, in, out, stream, true);
+}
+
+gbdct_status gbdct_exec_step(gbdct_plan_t plan, int inverse, int step, const void* in, void* out, void* stream) {
+  if (!plan || step < 0 || step >= gbdct_plan_launches_per_exec(plan)) return GBDCT_ERR_INVALID_ARG;
+  return exec2d(plan, in, out, stream, inverse != 0, step);
+}
+
+const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step) {
+  if (!plan || step < 0 || step >= gbdct_plan_launches_per_exec(plan)) return "";
+  static const char* kFwd2[] = {"column pass (reorder + column FFT + split)",
+                                "row pass (row FFT + symmetric-pair postprocess)"};
+  static const char* kInv2[] = {"row pass (four-read preprocess + row IFFT)",
+                                "column pass (column IFFT + inverse reorder)"};
+  static const char* kFwd3[] = {"column step C1 (reorder + DFT_B + twiddle)", "column step C2 (DFT_A)",
+                                "row pass (split + row FFT + postprocess)"};
+  static const char* kInv3[] = {"row pass (preprocess + row IFFT + pairing)", "column step C2' (DFT_A + twiddle)",
+                                "column step C1' (DFT_B + inverse reorder)"};
+  const bool three = plan->family == FAM_FS || plan->family == FAM_FSP;
+  int k = step;
+  if (plan->kind != GBDCT_DCT2) {
+    if (k == 0) return "index/sign map (pre)";
+    if (k == gbdct_plan_launches_per_exec(plan) - 1) return "index/sign map (post)";
+    k -= 1;
+  }
+  if (three) return inverse ? kInv3[k] : kFwd3[k];
+  return inverse ? kInv2[k] : kFwd2[k];
 }
 
 size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_bytes : 0; }

@@ -26,14 +26,15 @@ cudaError_t fs_impl(bool inverse, const Dct2dArgs& a, const float2* fstw, int ba
     if (e == cudaSuccess) e = set_smem(k_fs_inv_rows<N1, N2>, R::SMEM);
     return e;
   }
+  const int f = a.step_filter;
   if (!inverse) {
-    k_fs_fwd_c1<N1><<<g1, kFsCols, G::SMEM, s>>>(a, fstw);
-    k_fs_c2<N1, false><<<g2, kFsCols, G::SMEM, s>>>(a, fstw);
-    k_fs_fwd_rows<N1, N2><<<gr, R::THREADS, R::SMEM, s>>>(a);
+    if (f < 0 || f == 0) k_fs_fwd_c1<N1><<<g1, kFsCols, G::SMEM, s>>>(a, fstw);
+    if (f < 0 || f == 1) k_fs_c2<N1, false><<<g2, kFsCols, G::SMEM, s>>>(a, fstw);
+    if (f < 0 || f == 2) k_fs_fwd_rows<N1, N2><<<gr, R::THREADS, R::SMEM, s>>>(a);
   } else {
-    k_fs_inv_rows<N1, N2><<<gr, R::THREADS, R::SMEM, s>>>(a);
-    k_fs_c2<N1, true><<<g2, kFsCols, G::SMEM, s>>>(a, fstw);
-    k_fs_inv_c1<N1><<<g1, kFsCols, G::SMEM, s>>>(a);
+    if (f < 0 || f == 0) k_fs_inv_rows<N1, N2><<<gr, R::THREADS, R::SMEM, s>>>(a);
+    if (f < 0 || f == 1) k_fs_c2<N1, true><<<g2, kFsCols, G::SMEM, s>>>(a, fstw);
+    if (f < 0 || f == 2) k_fs_inv_c1<N1><<<g1, kFsCols, G::SMEM, s>>>(a);
   }
   return cudaGetLastError();
 }

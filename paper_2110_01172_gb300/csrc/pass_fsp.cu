@@ -33,14 +33,16 @@ cudaError_t fsp_impl(bool inverse, const Dct2dArgs& a, int batch, int nsm, cudaS
     if (e == cudaSuccess) e = pipe_launch<FsRowOp<N1, N2, true>>(a, 0, 0, 0, s, true);
     return e;
   }
+  const int f = a.step_filter;
   if (!inverse) {
-    e = pipe_launch<FsColOp<N1, 0>>(a, nA, batch, nsm, s, false);
-    if (e == cudaSuccess) e = pipe_launch<FsColOp<N1, 1>>(a, nB, batch, nsm, s, false);
-    if (e == cudaSuccess) e = pipe_launch<FsRowOp<N1, N2, false>>(a, nR, batch, nsm, s, false);
+    if (f < 0 || f == 0) e = pipe_launch<FsColOp<N1, 0>>(a, nA, batch, nsm, s, false);
+    if (e == cudaSuccess && (f < 0 || f == 1)) e = pipe_launch<FsColOp<N1, 1>>(a, nB, batch, nsm, s, false);
+    if (e == cudaSuccess && (f < 0 || f == 2))
+      e = pipe_launch<FsRowOp<N1, N2, false>>(a, nR, batch, nsm, s, false);
   } else {
-    e = pipe_launch<FsRowOp<N1, N2, true>>(a, nR, batch, nsm, s, false);
-    if (e == cudaSuccess) e = pipe_launch<FsColOp<N1, 2>>(a, nB, batch, nsm, s, false);
-    if (e == cudaSuccess) e = pipe_launch<FsColOp<N1, 3>>(a, nA, batch, nsm, s, false);
+    if (f < 0 || f == 0) e = pipe_launch<FsRowOp<N1, N2, true>>(a, nR, batch, nsm, s, false);
+    if (e == cudaSuccess && (f < 0 || f == 1)) e = pipe_launch<FsColOp<N1, 2>>(a, nB, batch, nsm, s, false);
+    if (e == cudaSuccess && (f < 0 || f == 2)) e = pipe_launch<FsColOp<N1, 3>>(a, nA, batch, nsm, s, false);
   }
   return e;
 }

@@ -88,6 +88,9 @@ class _Resources:
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph, stream=side):
                 self.solver.solve(self.rho, self.out[0], self.out[1], self.out[2], stream=side)
+            # the first launch of an instantiated graph uploads it to the device;
+            # do it here so that no request pays for it
+            self.graph.replay()
             torch.cuda.synchronize(device)
 
     def launch(self, rho_host, stream):

@@ -217,3 +217,27 @@ def test_small_families_full_oracle(family, shape, monkeypatch):
     torch.cuda.synchronize()
     check(X.cpu().numpy(), oracle.dct2_2d(x))
     check(y.cpu().numpy(), oracle.idct2_2d(X.cpu().numpy()))
+
+
+@pytest.mark.parametrize("family", ["pair", "fs", "fsp", "seq"])
+def test_single_steps_compose_to_the_full_transform(family, monkeypatch):
+    """gbdct_exec_step run for every launch in order equals the full call."""
+    shape = (1024, 4096)
+    if not FAMILY_SUPPORT[family](shape):
+        pytest.skip(f"{family} does not support {shape}")
+    monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
+    from paper_2110_01172_gb300 import Plan
+    plan = Plan(shape, "dct2")
+    x = torch.from_numpy(inputs.uniform(shape, seed=8)).cuda()
+    full = plan.forward(x)
+    stepped = torch.empty_like(x)
+    for k in range(plan.launches_per_exec):
+        assert plan.step_name(False, k)
+        plan.step(False, k, x, stepped)
+    torch.cuda.synchronize()
+    assert torch.equal(full, stepped)
+    back = torch.empty_like(x)
+    for k in range(plan.launches_per_exec):
+        plan.step(True, k, full, back)
+    torch.cuda.synchronize()
+    assert torch.equal(back, plan.inverse(full))
