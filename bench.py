@@ -49,12 +49,15 @@ FALLBACK_HBM_GBS = 6800.0
 # from the ncu capture summarised in profiles/, valid only for the kernel
 # sources with this digest (otherwise reported as null).
 TRAFFIC = {
-    "sources_sha256": "1f9e4d7a440fa9d4eaef81d83202c488b30bf57f5d05a43de4897d18cdd53cf4",
-    "bytes_per_launch": {   # profiles/pair_kernels_4096_ncu.md (cold L2 under ncu)
-        "forward column pass (reorder + column FFT + split)": 67285504 + 19485184,
-        "forward row pass (row FFT + symmetric-pair postprocess)": 67225088 + 18865664,
-        "inverse row pass (four-read preprocess + row IFFT)": 67237632 + 20116480,
-        "inverse column pass (column IFFT + inverse reorder)": 70111232 + 21584128,
+    "sources_sha256": "ff18c643529afad45ad92d970888359599607c7633ae1ea4b4a8782007f499ff",
+    "family": "fs2",
+    "bytes_per_launch": {   # profiles/fs2_kernels_4096_ncu.md (cold L2 under ncu)
+        "forward column step C1 (reorder + DFT_B + twiddle)": 67163648 + 17660672,
+        "forward column step C2 (DFT_A)": 67122432 + 6854144,
+        "forward row pass (split + row FFT + postprocess)": 67222528 + 17004032,
+        "inverse row pass (preprocess + row IFFT + pairing)": 67224576 + 15966208,
+        "inverse column step C2' (DFT_A + twiddle)": 67156736 + 6844672,
+        "inverse column step C1' (DFT_B + inverse reorder)": 67127040 + 17150720,
     },
 }
 
@@ -274,13 +277,17 @@ def run_serving(args, dev):
     """Poisson-arrival spectral Poisson solves: continuous batching vs one at a time."""
     import torch
     from paper_2110_01172_gb300.serving import (PoissonServer, _Resources, latency_summary, make_requests,
-                                                serve_plain)
+                                                serve_plain, touch_requests)
     n = args.serve_requests
     sets = {rate: make_requests(n, rate, seed=int(rate)) for rate in SERVE_RATES}
+    for reqs in sets.values():
+        touch_requests(reqs, dev.index)
     shapes = sorted({tuple(r.rho.shape) for reqs in sets.values() for r in reqs})
     server = PoissonServer(slots=8, device=dev.index)
-    server.warm(shapes, per_shape=2)
-    server.serve(make_requests(64, 1e6, seed=1))   # first use of every code path
+    server.warm(shapes, per_shape=8)   # one resident solver per slot and shape: no creation mid-run
+    burst = make_requests(64, 1e6, seed=1)
+    touch_requests(burst, dev.index)
+    server.serve(burst)   # first use of every code path
     solvers = {sh: _Resources(sh, dev) for sh in shapes}
     out = {"requests_per_rate": n, "slots": 8, "sizes": "N1, N2 in {64, ..., 2048}, 100-2000 blobs",
            "rates": []}
@@ -392,7 +399,7 @@ def run_ours(args):
     dom = max(kernels, key=lambda k: k["us"])
     achieved = algo_bytes / (dom["us"] * 1e-6) / 1e9
     traffic = None
-    if TRAFFIC["sources_sha256"] == sources_digest() and plan.family == "pair" and (n1, n2) == (4096, 4096):
+    if TRAFFIC["sources_sha256"] == sources_digest() and plan.family == TRAFFIC["family"] and (n1, n2) == (4096, 4096):
         traffic = TRAFFIC["bytes_per_launch"].get(dom["name"])
     launches = plan.launches_per_exec
 

@@ -130,10 +130,10 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan);
 /* Number of kernel launches one exec call issues (0 for a NULL plan). */
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
 
-/* Name of the kernel family the plan runs ("seq", "pair", "r64", "fs" or "fsp"; "" for a
+/* Name of the kernel family the plan runs ("seq", "pair", "r64", "fs", "fsp" or "fs2"; "" for a
  * NULL plan).  Every family computes the same transform; the plan picks the
  * fastest one that supports the shape, and the environment variable
- * GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp, read at plan creation, forces a family
+ * GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp|fs2, read at plan creation, forces a family
  * when it supports the shape (for testing and comparison). */
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
 

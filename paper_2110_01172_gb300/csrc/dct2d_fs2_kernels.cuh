@@ -1,0 +1,355 @@
+// dct2d_fs2_kernels.cuh - four-step column FFTs + row passes, occupancy-first.
+//
+// Same method and data flow as dct2d_fs_kernels.cuh (arXiv 2110.01172,
+// Algorithm 2 with the fused pre/postprocess of Section III; the column FFT of
+// length N1 = A*B split the four-step way so that every global access is a
+// contiguous row segment), with kernels shaped for occupancy:
+//
+//  * column steps: a CTA owns a slab of S rows (S = A or B) x 128 complex
+//    columns and 512 threads; the four threads of a column each hold T = S/4
+//    points, so a DFT_S is a DFT_T in registers, a twiddle W_S^{q m}, an
+//    exchange through shared memory and DFT4s (S = 4T:
+//    W_S^{(q+4j)(m+Tp)} = W_S^{qm} W_4^{qp} W_T^{jm});
+//  * row passes: one sequence per 16-point thread group (float2), the radix-16
+//    Stockham engine of fft_core.cuh, ~64 registers per thread.
+//
+// Workspace layout as in dct2d_fs_kernels.cuh: N1 rows of N2/2 complex, row
+// k1 of the column spectrum at physical row (k1 % B) * A + k1 / B.
+// Supported: N1 in {256, ..., 4096}, N2 in {256, ..., 16384}.
+#pragma once
+
+#include "dct2d_kernels.cuh"
+#include "fft_r64.cuh"
+
+namespace gbdct {
+
+constexpr int kCsCols = 128;            // complex columns per column-step CTA
+constexpr int kCsThreads = 4 * kCsCols;  // four threads per column
+
+template <int N1>
+struct Fs2Geom {
+  static constexpr int A = (N1 >= 2048) ? 64 : (N1 >= 512 ? 32 : 16);
+  static constexpr int B = N1 / A;
+};
+
+// Physical workspace row of column-spectrum row k1 (A, B powers of two).
+__device__ __forceinline__ int fs2_prow(int k1, int A, int B) { return (k1 & (B - 1)) * A + k1 / B; }
+
+// Multiplies X[m] (m < T) by W_S^{q m} for the thread's runtime q in [0, 4)
+// (q is uniform across a warp, so the switch does not diverge).
+template <int S, bool INV>
+__device__ __forceinline__ void cs_twiddle(float2* X, int q) {
+  constexpr int T = S / 4;
+  switch (q) {
+    case 1: r64::static_for<1, T>([&](auto mc) { constexpr int m = decltype(mc)::value; X[m] = r64::mul_w<S, 1 * m, INV>(X[m]); }); break;
+    case 2: r64::static_for<1, T>([&](auto mc) { constexpr int m = decltype(mc)::value; X[m] = r64::mul_w<S, 2 * m, INV>(X[m]); }); break;
+    case 3: r64::static_for<1, T>([&](auto mc) { constexpr int m = decltype(mc)::value; X[m] = r64::mul_w<S, 3 * m, INV>(X[m]); }); break;
+    default: break;
+  }
+}
+
+// DFT_S along the slab rows for the thread's column: on entry x[j] = row q + 4j
+// (j < T); on return y[i * 4 + p] = output row (q*T/4 + i) + T p  (i < T/4, p < 4).
+// `ex` is the CTA's S x 128 exchange buffer; contains one __syncthreads pair.
+template <int S, bool INV>
+__device__ __forceinline__ void cs_dft(float2* x, int q, int c, float2* ex) {
+  constexpr int T = S / 4;
+  r64::dft<T, INV>(x);
+  cs_twiddle<S, INV>(x, q);
+#pragma unroll
+  for (int m = 0; m < T; ++m) ex[(q * T + m) * kCsCols + c] = x[m];
+  __syncthreads();
+  constexpr int TQ = T / 4;  // m values per thread
+#pragma unroll
+  for (int i = 0; i < TQ; ++i) {
+    const int m = q * TQ + i;
+    float2 a0 = ex[(0 * T + m) * kCsCols + c], a1 = ex[(1 * T + m) * kCsCols + c];
+    float2 a2 = ex[(2 * T + m) * kCsCols + c], a3 = ex[(3 * T + m) * kCsCols + c];
+    dft4<INV>(a0, a1, a2, a3);
+    x[i * 4 + 0] = a0;
+    x[i * 4 + 1] = a1;
+    x[i * 4 + 2] = a2;
+    x[i * 4 + 3] = a3;
+  }
+  __syncthreads();
+}
+
+// Output slab row of register y[i*4 + p] (see cs_dft).
+template <int S>
+__device__ __forceinline__ int cs_out_row(int q, int i, int p) {
+  return q * (S / 16) + i + (S / 4) * p;
+}
+
+// ----------------------------------------------------------------------------
+// Column steps.  KIND 0: forward C1 (x rows -> DFT_B -> W_N1 twiddle)
+//                KIND 1: forward C2 (DFT_A in place)
+//                KIND 2: inverse C2' (IDFT_A, conj W_N1 twiddle, in place)
+//                KIND 3: inverse C1' (IDFT_B -> output rows, inverse reorder)
+// blockIdx.x = slab (n1a for KIND 0/3, k1b for KIND 1/2), blockIdx.y = column
+// block, blockIdx.z = batch.
+// ----------------------------------------------------------------------------
+template <int N1, int KIND>
+__global__ void __launch_bounds__(kCsThreads, 2)
+k_fs2_col(Dct2dArgs a) {
+  using G = Fs2Geom<N1>;
+  constexpr bool INV = KIND >= 2;
+  constexpr int S = (KIND == 0 || KIND == 3) ? G::B : G::A;
+  constexpr int T = S / 4;
+  extern __shared__ float4 scs[];
+  float2* ex = reinterpret_cast<float2*>(scs);
+  const int c = threadIdx.x % kCsCols, q = threadIdx.x / kCsCols;
+  const int r = blockIdx.x, cb = blockIdx.y;
+  const int N2 = a.n2;
+  const long long half = N2 / 2;  // complex per workspace row
+  const int col = cb * kCsCols + c;
+  float2* W = a.work + (long long)blockIdx.z * a.work_bstride;
+
+  float2 x[T];
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    const int i = q + 4 * j;  // slab row of this input
+    const float2* src;
+    if constexpr (KIND == 0) {
+      const float* xin = a.in + (long long)blockIdx.z * a.in_bstride;
+      src = reinterpret_cast<const float2*>(xin + (long long)reorder_src(r + G::A * i, N1) * N2) + col;
+    } else if constexpr (KIND == 3) {
+      src = W + (long long)(i * G::A + r) * half + col;
+    } else {
+      src = W + (long long)(r * G::A + i) * half + col;
+    }
+    x[j] = *src;
+  }
+  cs_dft<S, INV>(x, q, c, ex);
+#pragma unroll
+  for (int i = 0; i < T / 4; ++i)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int o = cs_out_row<S>(q, i, p);  // k1b (KIND 0), k1a (1), n1a (2), n1b (3)
+      float2 y = x[i * 4 + p];
+      if constexpr (KIND == 0) {
+        y = cmul(y, __ldg(a.fstw + r * G::B + o));
+        W[(long long)(o * G::A + r) * half + col] = y;
+      } else if constexpr (KIND == 2) {
+        y = cmulc(y, __ldg(a.fstw + o * G::B + r));
+        W[(long long)(r * G::A + o) * half + col] = y;
+      } else if constexpr (KIND == 1) {
+        W[(long long)(r * G::A + o) * half + col] = y;
+      } else {
+        float* xo = a.out + (long long)blockIdx.z * a.out_bstride;
+        *(reinterpret_cast<float2*>(xo + (long long)reorder_src(r + G::A * o, N1) * N2) + col) = y;
+      }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Forward row pass (L = N2): split in the loads, row FFT, symmetric-pair
+// postprocess (Section III-B, Eqs. four-elements, s-t).  Item k1 in [0, N1/2):
+// row k1 >= 1 gives output rows k1 and N1-k1; item 0 is the packed pair
+// V1(0,.) + i V1(N1/2,.) and gives rows 0 and N1/2.
+// ----------------------------------------------------------------------------
+template <int L>
+struct RowGeom {
+  static constexpr int TPS = fft_tps(L);
+  static constexpr int NI = (256 / TPS) > 0 ? 256 / TPS : 1;  // items per CTA
+  static constexpr int THREADS = NI * TPS;
+  static constexpr int LP = pad_len<float2>(L);
+  static constexpr size_t SMEM = (size_t)NI * LP * sizeof(float2);
+  static constexpr int MINB = 1024 / THREADS;  // caps registers at 64 per thread
+};
+
+// Copies two rows of L floats (row0 -> sf[0, L), row1 -> sf[L, 2L)) into shared
+// memory with 16-byte loads; TPS threads of one item, L/16 ... L/2 float4 each.
+template <int L, int TPS>
+__device__ __forceinline__ void stage_two_rows(float* sf, const float* row0, const float* row1, int g) {
+  const float4* a4 = reinterpret_cast<const float4*>(row0);
+  const float4* b4 = reinterpret_cast<const float4*>(row1);
+  float4* s4 = reinterpret_cast<float4*>(sf);
+  constexpr int Q = L / 4;  // float4 per row
+  float4 t[2 * Q / TPS];
+#pragma unroll
+  for (int j = 0; j < Q / TPS; ++j) {
+    t[j] = a4[g + j * TPS];
+    t[Q / TPS + j] = b4[g + j * TPS];
+  }
+#pragma unroll
+  for (int j = 0; j < Q / TPS; ++j) {
+    s4[g + j * TPS] = t[j];
+    s4[Q + g + j * TPS] = t[Q / TPS + j];
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::MINB)
+k_fs2_fwd_rows(Dct2dArgs a) {
+  const int N1 = a.n1;
+  using R = RowGeom<L>;
+  extern __shared__ float4 srw[];
+  const int li = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
+  float2* s = reinterpret_cast<float2*>(srw) + li * R::LP;
+  const int k1 = blockIdx.x * R::NI + li;
+  const bool packed = (k1 == 0);
+  const int kmir = packed ? N1 / 2 : N1 - k1;
+  const float2* Zw = a.work + (long long)blockIdx.z * a.work_bstride;
+  const float2* za_row = Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2);
+  const float2* zb_row = Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2);
+  float* y = a.out + (long long)blockIdx.z * a.out_bstride;
+
+  // both workspace rows (L/2 complex each) into the item's FFT buffer, raw
+  // layout, then the split reads them from there
+  stage_two_rows<L, R::TPS>(reinterpret_cast<float*>(s), reinterpret_cast<const float*>(za_row),
+                            reinterpret_cast<const float*>(zb_row), g);
+  __syncthreads();
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int n2 = g + j * R::TPS;
+    const bool lowhalf = n2 < L / 2;
+    const int p = lowhalf ? n2 : L - 1 - n2;
+    const float2 za = s[p];
+    const float2 zb = s[L / 2 + p];
+    if (packed) {
+      v[j] = lowhalf ? make_float2(za.x, zb.x) : make_float2(za.y, zb.y);
+    } else {
+      v[j] = lowhalf ? make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y))
+                     : make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+    }
+  }
+  __syncthreads();
+  first_stage_regs<L, false>(v, s, g);
+  __syncthreads();
+  fft_stages<L, 16, false>(s, g, a.tw2);
+
+  const float2 av = __ldg(a.fa + k1);
+  float* row0 = y + (long long)k1 * L;
+  float* row1 = y + (long long)kmir * L;
+  constexpr float RH = 0.70710678118654752f;
+  for (int i = g; i < L / 8; i += R::TPS) {
+    const int c = 4 * i;
+    float2 Yq[5], Ym[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      Yq[d] = s[pidx<float2>(c + d)];
+      Ym[d] = s[pidx<float2>((L - c - d) & (L - 1))];
+    }
+    float q0[4], q1[4], r0[4], r1[4];
+#pragma unroll
+    for (int d = 1; d <= 3; ++d) {
+      const float2 bt = __ldg(a.fb + c + d);
+      const float2 P = Yq[d], M = Ym[d];
+      if (packed) {
+        const float2 s0 = cmul(bt, make_float2(P.x + M.x, P.y - M.y));
+        const float2 sh = cmul(bt, make_float2(RH * (P.y + M.y), RH * (M.x - P.x)));
+        q0[d] = s0.x;
+        q1[d] = sh.x;
+        r0[4 - d] = -s0.y;
+        r1[4 - d] = -sh.y;
+      } else {
+        const float2 aP = cmul(P, av);
+        const float2 aM = cmul(M, av);
+        const float2 sv = cmul(bt, make_float2(aP.x + aM.x, aP.y - aM.y));
+        const float2 tv = cmul(bt, make_float2(aP.x - aM.x, aP.y + aM.y));
+        q0[d] = sv.x;
+        q1[d] = -tv.y;
+        r0[4 - d] = -sv.y;
+        r1[4 - d] = -tv.x;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int col = e ? (L - c - 4) : c;
+      const float2 P = e ? Ym[4] : Yq[0];
+      const float2 M = e ? Yq[4] : Ym[0];
+      const float2 bt = __ldg(a.fb + col);
+      float o0, o1;
+      if (packed) {
+        const float2 s0 = cmul(bt, make_float2(P.x + M.x, P.y - M.y));
+        const float2 sh = cmul(bt, make_float2(RH * (P.y + M.y), RH * (M.x - P.x)));
+        o0 = s0.x;
+        o1 = sh.x;
+      } else {
+        const float2 aP = cmul(P, av);
+        const float2 aM = cmul(M, av);
+        const float2 u = make_float2(aP.x + aM.x, aP.y - aM.y);
+        const float2 w = make_float2(aP.x - aM.x, aP.y + aM.y);
+        o0 = bt.x * u.x - bt.y * u.y;
+        o1 = -(bt.x * w.y + bt.y * w.x);
+      }
+      if (e) { r0[0] = o0; r1[0] = o1; } else { q0[0] = o0; q1[0] = o1; }
+    }
+    *reinterpret_cast<float4*>(row0 + c) = make_float4(q0[0], q0[1], q0[2], q0[3]);
+    *reinterpret_cast<float4*>(row1 + c) = make_float4(q1[0], q1[1], q1[2], q1[3]);
+    *reinterpret_cast<float4*>(row0 + L - c - 4) = make_float4(r0[0], r0[1], r0[2], r0[3]);
+    *reinterpret_cast<float4*>(row1 + L - c - 4) = make_float4(r1[0], r1[1], r1[2], r1[3]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Inverse row pass (L = N2): four-read preprocess (Eq. 2d_idct_pre, conjugated
+// twiddle, 1/(N1 N2) in the a-table) + row IFFT + column pairing
+// Z_p(k1) = U(k1,p) + i U(k1,L-1-p), Z_p(N1-k1) = conj(...).
+// ----------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::MINB)
+k_fs2_inv_rows(Dct2dArgs a) {
+  const int N1 = a.n1;
+  using R = RowGeom<L>;
+  extern __shared__ float4 srw[];
+  const int li = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
+  float2* s = reinterpret_cast<float2*>(srw) + li * R::LP;
+  const int k1 = blockIdx.x * R::NI + li;
+  const bool packed = (k1 == 0);
+  const int kmir = packed ? N1 / 2 : N1 - k1;
+  const float* C = a.in + (long long)blockIdx.z * a.in_bstride;
+  const float* ca = C + (long long)k1 * L;
+  const float* cb = C + (long long)kmir * L;
+  float2* Zw = a.work + (long long)blockIdx.z * a.work_bstride;
+  const float2 ia = __ldg(a.ia + k1);
+  const float2 ih = __ldg(a.ia + N1 / 2);
+
+  // rows k1 and kmir of C into the item's FFT buffer (raw layout), then the
+  // four-read preprocess reads them from there
+  const float* sf = reinterpret_cast<const float*>(s);
+  stage_two_rows<L, R::TPS>(reinterpret_cast<float*>(s), ca, cb, g);
+  __syncthreads();
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int k2 = g + j * R::TPS;
+    const int km = (L - k2) & (L - 1);
+    const float c1 = sf[k2], c3 = sf[L + k2];
+    const float c4 = k2 ? sf[km] : 0.f;
+    const float c2 = k2 ? sf[L + km] : 0.f;
+    const float2 bk = __ldg(a.ib + k2);
+    if (packed) {
+      const float2 v0 = cmul(cmul(make_float2(c1, -c4), bk), ia);
+      const float2 vh = cmul(cmul(make_float2(c3 - c2, -(c3 + c2)), bk), ih);
+      v[j] = make_float2(v0.x - vh.y, v0.y + vh.x);
+    } else {
+      v[j] = cmul(cmul(make_float2(c1 - c2, -(c3 + c4)), bk), ia);
+    }
+  }
+  __syncthreads();
+  first_stage_regs<L, true>(v, s, g);
+  __syncthreads();
+  fft_stages<L, 16, true>(s, g, a.tw2);
+
+  float2* zr0 = Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2);
+  float2* zr1 = Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2);
+  for (int h = g; h < L / 4; h += R::TPS) {  // two columns p = 2h, 2h + 1 per 16-byte store
+    const int p = 2 * h;
+    const float2 u0 = s[pidx<float2>(p)], u1 = s[pidx<float2>(p + 1)];
+    const float2 w0 = s[pidx<float2>(L - 1 - p)], w1 = s[pidx<float2>(L - 2 - p)];
+    float4 o0, o1;
+    if (packed) {
+      o0 = make_float4(u0.x, w0.x, u1.x, w1.x);
+      o1 = make_float4(u0.y, w0.y, u1.y, w1.y);
+    } else {
+      o0 = make_float4(u0.x - w0.y, u0.y + w0.x, u1.x - w1.y, u1.y + w1.x);
+      o1 = make_float4(u0.x + w0.y, w0.x - u0.y, u1.x + w1.y, w1.x - u1.y);
+    }
+    *reinterpret_cast<float4*>(zr0 + p) = o0;
+    *reinterpret_cast<float4*>(zr1 + p) = o1;
+  }
+}
+
+}  // namespace gbdct

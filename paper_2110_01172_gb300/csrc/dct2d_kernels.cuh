@@ -56,6 +56,7 @@ struct Dct2dArgs {
   const float2* fstw; // four-step twiddles W_N1^{n1a k1b} (four-step family only)
   int* err;           // device error word: set to 1 by a bounded wait that gave up
   int step_filter;    // host side only: -1 runs every launch, k runs launch k alone
+  int fsA, fsB;       // four-step split N1 = A * B (four-step families)
 };
 
 template <int L>

@@ -24,8 +24,8 @@ struct gbdct_plan_s {
   size_t work_bytes;
   Dct2dArgs args;   // pointers and sizes shared by all passes
   int b_cols, b_rows;  // sequences per CTA of the column and row passes
-  int family;          // kernel family: FAM_SEQ, FAM_PAIR, FAM_R64 or FAM_FS
-  float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS, FAM_FSP)
+  int family;          // kernel family (FAM_*)
+  float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS, FAM_FSP, FAM_FS2)
   int* err;            // device error word (bounded waits that gave up)
   int nsm;             // multiprocessors of the plan's device
   float* tmp;          // variant kinds: staging array (batch * N1 * N2 floats)
@@ -35,12 +35,14 @@ struct gbdct_plan_s {
 namespace {
 
 // Kernel families (all compute the same transform; chosen by size):
+//   FAM_FS2  four-step column steps (4 threads per column) + 16-point-per-thread
+//            row passes, N1 in {256..4096}, N2 in {256..16384}
 //   FAM_FSP  FAM_FS as persistent TMA-bulk-copy pipelines, N1 in {1024..4096}, N2 = 4096
 //   FAM_FS   four-step column FFTs + radix-64 rows, N1 in {1024..4096}, N2 in {4096, 8192}
 //   FAM_R64  radix-64 register FFTs, N1 and N2 in {4096, 8192}
 //   FAM_PAIR two interleaved sequences per thread, 16 <= N1, N2 <= 8192
 //   FAM_SEQ  one sequence per thread group, any supported size
-enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_R64 = 2, FAM_FS = 3, FAM_FSP = 4 };
+enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_R64 = 2, FAM_FS = 3, FAM_FSP = 4, FAM_FS2 = 5 };
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int64_t v) {
@@ -215,10 +217,13 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   const bool fs = p->lg1 >= gbdct::kFsMinLog2N1 && p->lg1 <= gbdct::kFsMaxLog2N1 &&
                   p->lg2 >= gbdct::kFsMinLog2N2 && p->lg2 <= gbdct::kFsMaxLog2N2;
   const bool fsp = fs && p->lg2 == 12;
-  // Default: the two-sequence family wherever it applies (fastest measured so
-  // far); the radix-64 and four-step families are opt-in below.
-  p->family = pair ? FAM_PAIR : FAM_SEQ;
-  // GBDCT_KERNEL_FAMILY=seq|pair|r64 forces a family when it supports the shape
+  const bool fs2 = p->lg1 >= gbdct::kFs2MinLog2N1 && p->lg1 <= gbdct::kFs2MaxLog2N1 &&
+                   p->lg2 >= gbdct::kFs2MinLog2N2 && p->lg2 <= gbdct::kFs2MaxLog2N2;
+  // Default: the occupancy-first four-step family where it applies, else the
+  // two-sequence family, else one sequence per thread group (fastest measured
+  // at every shape they share); the other families are opt-in below.
+  p->family = fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
+  // GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp|fs2 forces a family when it supports the shape
   // (used to test and compare every kernel family on the same inputs).
   if (const char* f = getenv("GBDCT_KERNEL_FAMILY")) {
     if (!strcmp(f, "seq")) p->family = FAM_SEQ;
@@ -226,9 +231,10 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
     else if (!strcmp(f, "r64") && r64) p->family = FAM_R64;
     else if (!strcmp(f, "fs") && fs) p->family = FAM_FS;
     else if (!strcmp(f, "fsp") && fsp) p->family = FAM_FSP;
+    else if (!strcmp(f, "fs2") && fs2) p->family = FAM_FS2;
   }
-  const bool four_step = p->family == FAM_FS || p->family == FAM_FSP;
-  p->pmax = (p->family == FAM_R64 || four_step) ? gbdct::r64::PMAX : 16;
+  const bool four_step = p->family == FAM_FS || p->family == FAM_FSP || p->family == FAM_FS2;
+  p->pmax = (p->family == FAM_R64 || p->family == FAM_FS || p->family == FAM_FSP) ? gbdct::r64::PMAX : 16;
 
   // Table layout, each block padded to 2 float2 (16 B).
   const int tot1 = gbdct::tw_size_p(n1, p->pmax), tot2 = gbdct::tw_size_p(n2, p->pmax);
@@ -265,10 +271,14 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   if (tot2 > 0) k_gen_stage_twiddles<<<(tot2 + 255) / 256, 256>>>(tw2, n2, p->pmax, tot2);
   const int nt = (n1 / 2 + 1 > n2) ? (n1 / 2 + 1) : n2;
   k_gen_dct_tables<<<(nt + 255) / 256, 256>>>(fa, fb, ia, ib, n1, n2);
-  if (p->fstw) {
-    const int A = (n1 == 1024) ? 32 : 64, B = n1 / A;
-    k_gen_fs_twiddles<<<(n1 + 255) / 256, 256>>>(p->fstw, n1, A, B);
+  int fsA = 0, fsB = 0;
+  if (p->family == FAM_FS2) {
+    gbdct::fs2_split(p->lg1, &fsA, &fsB);
+  } else if (p->fstw) {
+    fsA = (n1 == 1024) ? 32 : 64;
+    fsB = n1 / fsA;
   }
+  if (p->fstw) k_gen_fs_twiddles<<<(n1 + 255) / 256, 256>>>(p->fstw, n1, fsA, fsB);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemset(p->err, 0, 16);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
@@ -294,11 +304,15 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   a.fstw = p->fstw;
   a.err = p->err;
   a.step_filter = -1;
+  a.fsA = fsA;
+  a.fsB = fsB;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 
   // Raise the dynamic shared-memory limit of the kernels once.
-  if (p->family == FAM_FSP) {
+  if (p->family == FAM_FS2) {
+    e = gbdct::run_fs2(p->lg1, p->lg2, false, a, 1, 0, true);
+  } else if (p->family == FAM_FSP) {
     e = gbdct::run_fsp(p->lg1, p->lg2, false, a, 1, p->nsm, 0, true);
   } else if (p->family == FAM_FS) {
     e = gbdct::run_fs(p->lg1, p->lg2, false, a, p->fstw, 1, 0, true);
@@ -337,7 +351,9 @@ gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims,
 
 static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse,
                               int step = -1);
-static int core_launches(gbdct_plan_t p) { return (p->family == FAM_FS || p->family == FAM_FSP) ? 3 : 2; }
+static int core_launches(gbdct_plan_t p) {
+  return (p->family == FAM_FS || p->family == FAM_FSP || p->family == FAM_FS2) ? 3 : 2;
+}
 
 static cudaError_t run_map(gbdct_plan_t p, const float* in, float* out, MapSpec m, cudaStream_t s) {
   const dim3 grid((p->n2 + 255) / 256, p->n1, (unsigned)p->batch);
@@ -398,6 +414,9 @@ static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStr
   const int batch = (int)p->batch;
   const bool s0 = step < 0 || step == 0, s1 = step < 0 || step == 1;
   cudaError_t e = cudaSuccess;
+  if (p->family == FAM_FS2) {
+    return cuda_status(gbdct::run_fs2(p->lg1, p->lg2, inverse, a, batch, s, false));
+  }
   if (p->family == FAM_FSP) {
     return cuda_status(gbdct::run_fsp(p->lg1, p->lg2, inverse, a, batch, p->nsm, s, false));
   }
@@ -462,7 +481,7 @@ const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step) {
                                 "row pass (split + row FFT + postprocess)"};
   static const char* kInv3[] = {"row pass (preprocess + row IFFT + pairing)", "column step C2' (DFT_A + twiddle)",
                                 "column step C1' (DFT_B + inverse reorder)"};
-  const bool three = plan->family == FAM_FS || plan->family == FAM_FSP;
+  const bool three = core_launches(plan) == 3;
   int k = step;
   if (plan->kind != GBDCT_DCT2) {
     if (k == 0) return "index/sign map (pre)";
@@ -477,13 +496,13 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_
 
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (!plan) return 0;
-  const int core = (plan->family == FAM_FS || plan->family == FAM_FSP) ? 3 : 2;
+  const int core = core_launches(plan);
   return plan->kind == GBDCT_DCT2 ? core : core + 2;
 }
 
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
   if (!plan) return "";
-  return plan->family == FAM_FSP ? "fsp" : plan->family == FAM_FS ? "fs" : plan->family == FAM_R64 ? "r64" : plan->family == FAM_PAIR ? "pair" : "seq";
+  return plan->family == FAM_FS2 ? "fs2" : plan->family == FAM_FSP ? "fsp" : plan->family == FAM_FS ? "fs" : plan->family == FAM_R64 ? "r64" : plan->family == FAM_PAIR ? "pair" : "seq";
 }
 
 gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan) {

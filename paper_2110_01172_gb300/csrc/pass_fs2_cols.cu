@@ -1,0 +1,45 @@
+// pass_fs2_cols.cu - column steps of the occupancy-first four-step family.
+#include "dct2d_launch.cuh"
+
+namespace gbdct {
+namespace {
+
+template <int N1, int KIND>
+cudaError_t col_launch(const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  using G = Fs2Geom<N1>;
+  constexpr int S = (KIND == 0 || KIND == 3) ? G::B : G::A;
+  constexpr size_t smem = (size_t)S * kCsCols * sizeof(float2);
+  if (prepare) {
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_col<N1, KIND>),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  const int nslab = (KIND == 0 || KIND == 3) ? G::A : G::B;
+  k_fs2_col<N1, KIND><<<dim3(nslab, a.n2 / 2 / kCsCols, batch), kCsThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N1>
+cudaError_t cols_impl(int kind, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  switch (kind) {
+    case 0: return col_launch<N1, 0>(a, batch, s, prepare);
+    case 1: return col_launch<N1, 1>(a, batch, s, prepare);
+    case 2: return col_launch<N1, 2>(a, batch, s, prepare);
+    case 3: return col_launch<N1, 3>(a, batch, s, prepare);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t run_fs2_col(int lg1, int kind, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  switch (lg1) {
+    case 8: return cols_impl<256>(kind, a, batch, s, prepare);
+    case 9: return cols_impl<512>(kind, a, batch, s, prepare);
+    case 10: return cols_impl<1024>(kind, a, batch, s, prepare);
+    case 11: return cols_impl<2048>(kind, a, batch, s, prepare);
+    case 12: return cols_impl<4096>(kind, a, batch, s, prepare);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gbdct

@@ -149,10 +149,11 @@ FAMILY_SUPPORT = {
     "r64": lambda s: all(n in (4096, 8192) for n in s),
     "fs": lambda s: s[0] in (1024, 2048, 4096) and s[1] in (4096, 8192),
     "fsp": lambda s: s[0] in (1024, 2048, 4096) and s[1] == 4096,
+    "fs2": lambda s: 256 <= s[0] <= 4096 and 256 <= s[1] <= 16384,
 }
 
 
-@pytest.mark.parametrize("family", ["seq", "pair", "r64", "fs", "fsp"])
+@pytest.mark.parametrize("family", ["seq", "pair", "r64", "fs", "fsp", "fs2"])
 @pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192), (1024, 4096)])
 def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
     """Each kernel family, forced through GBDCT_KERNEL_FAMILY, on the same inputs."""
@@ -183,12 +184,13 @@ def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
     plan.close()
 
 
-def test_batched_pipelined_family(monkeypatch):
-    monkeypatch.setenv("GBDCT_KERNEL_FAMILY", "fsp")
+@pytest.mark.parametrize("family", ["fsp", "fs2"])
+def test_batched_four_step_families(family, monkeypatch):
+    monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
     from paper_2110_01172_gb300 import Plan, binding
     shape = (1024, 4096)
     plan = Plan(shape, "dct2", batch=2)
-    assert plan.family == "fsp"
+    assert plan.family == family
     xs = np.stack([inputs.uniform(shape, seed=s) for s in (31, 32)])
     X = plan.forward(torch.from_numpy(xs).cuda())
     y = plan.inverse(X)
@@ -202,8 +204,8 @@ def test_batched_pipelined_family(monkeypatch):
     assert plan.check_device_error() == binding.OK
 
 
-@pytest.mark.parametrize("family", ["seq", "pair"])
-@pytest.mark.parametrize("shape", [(256, 512), (64, 2048)])
+@pytest.mark.parametrize("family", ["seq", "pair", "fs2"])
+@pytest.mark.parametrize("shape", [(256, 512), (64, 2048), (256, 256), (512, 256), (2048, 256), (256, 16384)])
 def test_small_families_full_oracle(family, shape, monkeypatch):
     if not FAMILY_SUPPORT[family](shape):
         pytest.skip(f"{family} does not support {shape}")
@@ -219,7 +221,7 @@ def test_small_families_full_oracle(family, shape, monkeypatch):
     check(y.cpu().numpy(), oracle.idct2_2d(X.cpu().numpy()))
 
 
-@pytest.mark.parametrize("family", ["pair", "fs", "fsp", "seq"])
+@pytest.mark.parametrize("family", ["pair", "fs", "fsp", "seq", "fs2"])
 def test_single_steps_compose_to_the_full_transform(family, monkeypatch):
     """gbdct_exec_step run for every launch in order equals the full call."""
     shape = (1024, 4096)
