@@ -28,6 +28,8 @@ from .dct_oracle import (  # noqa: F401
     idxst_idct,
     dct2_3d,
     idct2_3d,
+    dct2_3d_entries,
+    idct2_3d_entries,
     dct2_2d_entries,
     idct2_2d_entries,
     poisson_solve,

@@ -33,6 +33,7 @@ __all__ = [
     "dct2_matrix", "dct3_inverse_matrix", "dst2_matrix", "dst2_inverse_matrix",
     "idxst_matrix", "dct2_1d", "idct_1d", "idxst_1d", "dct2_2d", "idct2_2d",
     "dst2_2d", "idst2_2d", "idct_idxst", "idxst_idct", "dct2_3d", "idct2_3d",
+    "dct2_3d_entries", "idct2_3d_entries",
     "dct2_2d_entries", "idct2_2d_entries", "poisson_solve", "compress_threshold",
 ]
 
@@ -246,6 +247,25 @@ def idct2_3d(x) -> np.ndarray:
     return np.einsum("ai,bj,ck,ijk->abc", dct3_inverse_matrix(n0),
                      dct3_inverse_matrix(n1), dct3_inverse_matrix(n2), x,
                      optimize=True)
+
+
+def dct2_3d_entries(x, k0, k1, k2) -> np.ndarray:
+    """Entries X[k0[i], k1[i], k2[i]] of ``dct2_3d(x)``, each as the triple sum
+    of x against the three cosine rows (for sizes too large for the full map)."""
+    x = _f64(x)
+    n0, n1, n2 = x.shape
+    c0, c1, c2 = dct2_matrix(n0), dct2_matrix(n1), dct2_matrix(n2)
+    return np.array([np.einsum("i,j,k,ijk->", c0[a], c1[b], c2[c], x, optimize=True)
+                     for a, b, c in zip(k0, k1, k2)])
+
+
+def idct2_3d_entries(x, n0_idx, n1_idx, n2_idx) -> np.ndarray:
+    """Entries of ``idct2_3d(x)`` at the given positions, as triple sums."""
+    x = _f64(x)
+    n0, n1, n2 = x.shape
+    d0, d1, d2 = dct3_inverse_matrix(n0), dct3_inverse_matrix(n1), dct3_inverse_matrix(n2)
+    return np.array([np.einsum("i,j,k,ijk->", d0[a], d1[b], d2[c], x, optimize=True)
+                     for a, b, c in zip(n0_idx, n1_idx, n2_idx)])
 
 
 # ---------------------------------------------------------------------------

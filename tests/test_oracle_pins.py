@@ -326,6 +326,32 @@ def test_dct3d_bruteforce_and_round_trip():
     np.testing.assert_allclose(oracle.idct2_3d(oracle.dct2_3d(y)), y, atol=1e-12)
 
 
+def test_3d_entries_helpers_match_brute_force_pinned_full_maps():
+    """The single-entry 3D helpers against the full maps (pinned above by the
+    sextuple loop and the round trip), including the corners and row N/2."""
+    x = inputs.uniform((8, 4, 16), seed=18)
+    X, Y = oracle.dct2_3d(x), oracle.idct2_3d(x)
+    k0 = np.array([0, 7, 4, 1, 0, 3])
+    k1 = np.array([0, 3, 2, 0, 1, 2])
+    k2 = np.array([0, 15, 8, 1, 15, 7])
+    np.testing.assert_allclose(oracle.dct2_3d_entries(x, k0, k1, k2), X[k0, k1, k2], atol=1e-11)
+    np.testing.assert_allclose(oracle.idct2_3d_entries(x, k0, k1, k2), Y[k0, k1, k2], atol=1e-12)
+
+
+def test_3d_separable_cosine_is_a_single_delta():
+    """cos(pi p (2a+1)/2N0) cos(pi q (2b+1)/2N1) cos(pi r (2c+1)/2N2) maps to one
+    nonzero coefficient (N0/2)(N1/2)(N2/2) (doubled per zero index)."""
+    n0, n1, n2, p, q, r = 4, 8, 2, 3, 0, 1
+    a = np.cos(np.pi * p * (2 * np.arange(n0) + 1) / (2 * n0))
+    b = np.cos(np.pi * q * (2 * np.arange(n1) + 1) / (2 * n1))
+    c = np.cos(np.pi * r * (2 * np.arange(n2) + 1) / (2 * n2))
+    x = np.einsum("i,j,k->ijk", a, b, c)
+    X = oracle.dct2_3d(x)
+    want = np.zeros_like(X)
+    want[p, q, r] = (n0 / 2) * (n1 / 2) * (n2 / 2) * (2 if p == 0 else 1) * (2 if q == 0 else 1) * (2 if r == 0 else 1)
+    np.testing.assert_allclose(X, want, atol=1e-12)
+
+
 def _cos_series(coef, t1, t2):
     """Evaluate sum_uv w c_uv cos(pi u (t1+1/2)/N1) cos(pi v (t2+1/2)/N2) off-grid.
 
