@@ -80,7 +80,12 @@ const char* gbdct_version(void);
  * FP32 (the paper's coefficients "fixed before the call", Section III-B), and
  * allocates its workspace (gbdct_plan_workspace_bytes).
  *   out   receives the plan handle (unchanged on error).
- *   ndim  2 (3 returns GBDCT_ERR_UNSUPPORTED in this build).
+ *   ndim  2, or 3 for the 3D DCT-II and its inverse (kind GBDCT_DCT2 only;
+ *         the triple separable sum, Section III-D).  A 3D plan of dims
+ *         (N0, N1, N2) runs the 2D transform of each of its N0 slices as one
+ *         batched 2D plan and a 1D pass along axis 0 (inverse: axis 0 first);
+ *         N0 must be a power of two between 2 and 4096 and batch * N0 at most
+ *         65535, else GBDCT_ERR_UNSUPPORTED.  ndim 1 gives UNSUPPORTED.
  *   dims  ndim sizes; each must be a power of two between 2 and 16384, else
  *         GBDCT_ERR_UNSUPPORTED (dims <= 0 give GBDCT_ERR_INVALID_ARG).
  *   kind  a gbdct_kind; dtype must be GBDCT_F32.  Kinds other than

@@ -294,6 +294,21 @@ def idct2(x, out=None):
     return _cached_plan(shape, "dct2", batch, x.device).inverse(x, out)
 
 
+def dct3(x, out=None):
+    """3D DCT-II (unnormalised, the 1D DCT-II along every axis) of a CUDA float32
+    (N0, N1, N2) tensor."""
+    if x.dim() != 3:
+        raise ValueError("expected a 3D tensor")
+    return _cached_plan(tuple(x.shape), "dct2", 1, x.device).forward(x, out)
+
+
+def idct3(x, out=None):
+    """Exact inverse of ``dct3``."""
+    if x.dim() != 3:
+        raise ValueError("expected a 3D tensor")
+    return _cached_plan(tuple(x.shape), "dct2", 1, x.device).inverse(x, out)
+
+
 def dst2(x, out=None):
     """2D DST-II (unnormalised sine analogue of ``dct2``)."""
     shape, batch = _split(x)

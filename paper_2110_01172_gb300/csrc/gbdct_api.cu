@@ -8,6 +8,7 @@
 
 #include "../../include/gbdct.h"
 #include "dct2d_launch.cuh"
+#include "dct_axis0.cuh"
 
 using gbdct::Dct2dArgs;
 
@@ -30,6 +31,14 @@ struct gbdct_plan_s {
   int nsm;             // multiprocessors of the plan's device
   float* tmp;          // variant kinds: staging array (batch * N1 * N2 floats)
   int pmax;            // points per thread of the stage structure (twiddle layout)
+  // ndim == 3 (N0, N1, N2): the 2D transforms of the N0 slices run as a batched
+  // 2D plan, then a 1D pass along axis 0 (inverse: axis 0 first).
+  gbdct_plan_t inner;  // batched 2D plan of the (N1, N2) slices (batch * N0 transforms)
+  float2* ax_tables;   // axis-0 stage twiddles, forward post and inverse pre tables
+  const float2* ax_fw; // e^{-i pi k / 2 N0} / 2
+  const float2* ax_iw; // e^{+i pi k / 2 N0} / N0
+  gbdct::AxisArgs ax;  // axis-0 pass arguments (in, out, w set per call)
+  int lg0;
 };
 
 namespace {
@@ -98,6 +107,18 @@ __global__ void k_gen_dct_tables(float2* fa, float2* fb, float2* ia, float2* ib,
   }
 }
 
+// Axis-0 tables of the 3D transform (FP64, k in [0, N)):
+//   fw[k] = e^{-i pi k / 2N} / 2   (forward post, Hermitian-split 1/2 folded in)
+//   iw[k] = e^{+i pi k / 2N} / N   (inverse pre, inverse DFT scale folded in)
+__global__ void k_gen_axis_tables(float2* fw, float2* iw, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double sn, cs;
+  sincospi((double)k / (2.0 * (double)n), &sn, &cs);
+  fw[k] = make_float2((float)(0.5 * cs), (float)(-0.5 * sn));
+  iw[k] = make_float2((float)(cs / n), (float)(sn / n));
+}
+
 // Four-step twiddles W_N1^{n1a k1b} at n1a * B + k1b (n1a < A, k1b < B), FP64.
 __global__ void k_gen_fs_twiddles(float2* out, int n1, int A, int B) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,6 +175,8 @@ struct DeviceGuard {
 
 void free_plan(gbdct_plan_s* p) {
   if (!p) return;
+  if (p->inner) gbdct_plan_destroy(p->inner);
+  if (p->ax_tables) cudaFree(p->ax_tables);
   if (p->tables) cudaFree(p->tables);
   if (p->work) cudaFree(p->work);
   if (p->tmp) cudaFree(p->tmp);
@@ -161,6 +184,91 @@ void free_plan(gbdct_plan_s* p) {
 }
 
 }  // namespace
+
+extern "C" {
+static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stream, bool inverse, int step);
+}
+
+static gbdct_status run_plan(gbdct_plan_t p, bool inverse, int step, const void* in, void* out,
+                                           cudaStream_t s) {
+  return exec2d(p, in, out, reinterpret_cast<void*>(s), inverse, step);
+}
+
+static gbdct_status create_3d(gbdct_plan_t* out, const int64_t* dims, int64_t batch, int kind, int dtype) {
+  if (kind != GBDCT_DCT2) return GBDCT_ERR_UNSUPPORTED;
+  for (int i = 0; i < 3; ++i)
+    if (!is_pow2(dims[i])) return GBDCT_ERR_UNSUPPORTED;
+  const int lg0 = ilog2(dims[0]);
+  if (lg0 < gbdct::kAxisMinLog2 || lg0 > gbdct::kAxisMaxLog2) return GBDCT_ERR_UNSUPPORTED;
+  if (batch * dims[0] > 65535) return GBDCT_ERR_UNSUPPORTED;
+  gbdct_plan_s* p = new (std::nothrow) gbdct_plan_s();
+  if (!p) return GBDCT_ERR_OOM;
+  p->ndim = 3;
+  for (int i = 0; i < 3; ++i) p->dims[i] = dims[i];
+  p->batch = batch;
+  p->kind = kind;
+  p->lg0 = lg0;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return GBDCT_ERR_CUDA;
+  }
+  gbdct_status st = gbdct_plan_create_batched(&p->inner, 2, dims + 1, batch * dims[0], GBDCT_DCT2, dtype);
+  if (st != GBDCT_OK) {
+    free_plan(p);
+    return st;
+  }
+  const int n0 = (int)dims[0];
+  const int tot = gbdct::tw_size_p(n0, 16);
+  const size_t t0 = round_up(tot + 1, 2), tn = round_up(n0, 2);
+  cudaError_t e = cudaMalloc(&p->ax_tables, (t0 + 2 * tn) * sizeof(float2));
+  if (e == cudaSuccess) {
+    float2* fw = p->ax_tables + t0;
+    float2* iw = fw + tn;
+    if (tot > 0) k_gen_stage_twiddles<<<(tot + 255) / 256, 256>>>(p->ax_tables, n0, 16, tot);
+    k_gen_axis_tables<<<(n0 + 255) / 256, 256>>>(fw, iw, n0);
+    p->ax_fw = fw;
+    p->ax_iw = iw;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  p->ax.M = dims[1] * dims[2];
+  p->ax.bstride = dims[0] * dims[1] * dims[2];
+  p->ax.tw = p->ax_tables;
+  p->ax.lgP = gbdct::axis0_lgP(lg0, p->ax.M);
+  if (e == cudaSuccess) e = gbdct::run_axis0(lg0, false, p->ax, 1, 0, true);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  p->work_bytes = gbdct_plan_workspace_bytes(p->inner);
+  p->family = p->inner->family;
+  *out = p;
+  return GBDCT_OK;
+}
+
+static gbdct_status exec3d(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse, int step) {
+  const int ni = gbdct_plan_launches_per_exec(p->inner);
+  gbdct::AxisArgs ax = p->ax;
+  ax.w = inverse ? p->ax_iw : p->ax_fw;
+  if (!inverse) {
+    if (step < 0 || step < ni) {
+      const gbdct_status st = run_plan(p->inner, false, step, in, out, s);
+      if (st != GBDCT_OK) return st;
+    }
+    if (step >= 0 && step != ni) return GBDCT_OK;
+    ax.in = static_cast<const float*>(out);
+    ax.out = static_cast<float*>(out);
+    return cuda_status(gbdct::run_axis0(p->lg0, false, ax, (int)p->batch, s, false));
+  }
+  if (step < 0 || step == 0) {
+    ax.in = static_cast<const float*>(in);
+    ax.out = static_cast<float*>(out);
+    const cudaError_t e = gbdct::run_axis0(p->lg0, true, ax, (int)p->batch, s, false);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (step == 0) return GBDCT_OK;
+  return run_plan(p->inner, true, step < 0 ? -1 : step - 1, out, out, s);
+}
 
 extern "C" {
 
@@ -186,6 +294,7 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
     if (dims[i] <= 0) return GBDCT_ERR_INVALID_ARG;
   if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
   if (dtype != GBDCT_F32) return GBDCT_ERR_UNSUPPORTED;
+  if (ndim == 3) return create_3d(out, dims, batch, kind, dtype);
   if (ndim != 2) return GBDCT_ERR_UNSUPPORTED;
   for (int i = 0; i < ndim; ++i) {
     if (!is_pow2(dims[i])) return GBDCT_ERR_UNSUPPORTED;
@@ -365,11 +474,12 @@ static cudaError_t run_map(gbdct_plan_t p, const float* in, float* out, MapSpec 
 //   DST-II(x)_k = DCT-II((-1)^n x)_{N-1-k} per axis (both axes);
 //   IDXST(x)_k = (-1)^k IDCT({x_{N-n}})_k, x_N = 0 (Section V-B, Eq. idxst).
 static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stream, bool inverse,
-                           int step = -1) {
+                           int step) {
   if (!p || !in || !out) return GBDCT_ERR_INVALID_ARG;
   if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return GBDCT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (p->ndim == 3) return exec3d(p, in, out, s, inverse, step);
   if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse, step);
   MapSpec pre{}, post{};
   if (p->kind == GBDCT_DST2) {
@@ -459,11 +569,11 @@ static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStr
 }
 
 gbdct_status gbdct_exec_forward(gbdct_plan_t plan, const void* in, void* out, void* stream) {
-  return exec2d(plan, in, out, stream, false);
+  return exec2d(plan, in, out, stream, false, -1);
 }
 
 gbdct_status gbdct_exec_inverse(gbdct_plan_t plan, const void* in, void* out, void* stream) {
-  return exec2d(plan, in, out, stream, true);
+  return exec2d(plan, in, out, stream, true, -1);
 }
 
 gbdct_status gbdct_exec_step(gbdct_plan_t plan, int inverse, int step, const void* in, void* out, void* stream) {
@@ -473,6 +583,13 @@ gbdct_status gbdct_exec_step(gbdct_plan_t plan, int inverse, int step, const voi
 
 const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step) {
   if (!plan || step < 0 || step >= gbdct_plan_launches_per_exec(plan)) return "";
+  if (plan->ndim == 3) {
+    const int ni = gbdct_plan_launches_per_exec(plan->inner);
+    if (!inverse) return step < ni ? gbdct_plan_step_name(plan->inner, 0, step)
+                                   : "axis-0 pass (reorder + column FFT + split + twiddle)";
+    return step == 0 ? "axis-0 pass (twiddle + column IFFT + inverse reorder)"
+                     : gbdct_plan_step_name(plan->inner, 1, step - 1);
+  }
   static const char* kFwd2[] = {"column pass (reorder + column FFT + split)",
                                 "row pass (row FFT + symmetric-pair postprocess)"};
   static const char* kInv2[] = {"row pass (four-read preprocess + row IFFT)",
@@ -496,6 +613,7 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_
 
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (!plan) return 0;
+  if (plan->ndim == 3) return gbdct_plan_launches_per_exec(plan->inner) + 1;
   const int core = core_launches(plan);
   return plan->kind == GBDCT_DCT2 ? core : core + 2;
 }
@@ -507,6 +625,7 @@ const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
 
 gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan) {
   if (!plan) return GBDCT_ERR_INVALID_ARG;
+  if (plan->ndim == 3) return gbdct_plan_check_device_error(plan->inner);
   DeviceGuard guard(plan->device);
   int v = 0;
   if (cudaMemcpy(&v, plan->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBDCT_ERR_CUDA;

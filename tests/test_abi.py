@@ -56,6 +56,12 @@ def _create(lib, dims, ndim=None, kind=0, dtype=0, batch=1):
     ((12, 8), None, 0, 0, 1, binding.ERR_UNSUPPORTED),       # not a power of two
     ((1, 8), None, 0, 0, 1, binding.ERR_UNSUPPORTED),        # below the smallest size
     ((8, 32768), None, 0, 0, 1, binding.ERR_UNSUPPORTED),    # above the largest size
+    ((8,), None, 0, 0, 1, binding.ERR_UNSUPPORTED),          # 1D
+    ((8, 8, 8), None, 1, 0, 1, binding.ERR_UNSUPPORTED),     # 3D: DCT-II only
+    ((12, 8, 8), None, 0, 0, 1, binding.ERR_UNSUPPORTED),    # 3D: not a power of two
+    ((8192, 8, 8), None, 0, 0, 1, binding.ERR_UNSUPPORTED),  # 3D: axis 0 above 4096
+    ((4096, 8, 8), None, 0, 0, 16, binding.ERR_UNSUPPORTED), # 3D: batch * N0 > 65535
+    ((8, 0, 8), None, 0, 0, 1, binding.ERR_INVALID_ARG),     # 3D: dim <= 0
 ])
 def test_plan_create_rejects_before_touching_the_gpu(lib, dims, ndim, kind, dtype, batch, expect):
     st, h = _create(lib, dims, ndim, kind, dtype, batch)
