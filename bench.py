@@ -73,6 +73,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the secondary configurations")
     ap.add_argument("--serve-requests", type=int, default=300)
     return ap.parse_args(argv)
 
@@ -299,6 +300,72 @@ def run_serving(args, dev):
     return out
 
 
+def _event_loop_us(fn, iters, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for i in range(3):
+        fn(i)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(iters):
+        fn(i)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / iters
+
+
+def run_configs(dev, peak):
+    """The other benchmark configurations (secondary lines; the headline is 4096^2):
+    C2 shapes, C3 (3D and the DST/IDXST kinds), C4 (512 uneven transforms under
+    a CUDA graph).  Two rotating buffer sets per shape; at >= 1024^2 the sets
+    exceed L2."""
+    import torch
+    from paper_2110_01172_gb300 import MultiPlan, Plan, inputs
+    stream = torch.cuda.current_stream(dev)
+    out = {"2d": [], "3d": [], "kinds_2048": [], "batched": None}
+
+    def one(shape, kind="dct2"):
+        plan = Plan(shape, kind)
+        n = 1
+        for v in shape:
+            n *= v
+        xs = [torch.rand(shape, device=dev) * 2 - 1 for _ in range(2)]
+        ys = [torch.empty_like(xs[0]) for _ in range(2)]
+        rec = {"shape": list(shape), "kind": kind, "family": plan.family}
+        if kind in ("dct2", "dst2"):
+            rec["fwd_us"] = _event_loop_us(lambda i: plan.forward(xs[i % 2], ys[i % 2]), 20, stream)
+            rec["fwd_frac"] = 8.0 * n / (rec["fwd_us"] * 1e-6) / 1e9 / peak
+        rec["inv_us"] = _event_loop_us(lambda i: plan.inverse(xs[i % 2], ys[i % 2]), 20, stream)
+        rec["inv_frac"] = 8.0 * n / (rec["inv_us"] * 1e-6) / 1e9 / peak
+        plan.close()
+        return rec
+
+    for shape in [(1024, 1024), (2048, 2048), (8192, 8192), (2048, 4096), (1024, 8192)]:
+        out["2d"].append(one(shape))
+    for shape in [(128, 128, 128), (256, 256, 256)]:
+        out["3d"].append(one(shape))
+    for kind in ("dst2", "idct_idxst", "idxst_idct"):
+        out["kinds_2048"].append(one((2048, 2048), kind))
+
+    shapes = inputs.batched_shapes(512, seed=0, lo=64, hi=1024)
+    rec = {"transforms": len(shapes), "sides": "log-uniform powers of two 64..1024, squares and 1:2 rectangles"}
+    for graph in (True, False):
+        m = MultiPlan(shapes, graph=graph)
+        xin = torch.rand(m.total, device=dev) * 2 - 1
+        mid, back = torch.empty_like(xin), torch.empty_like(xin)
+        key = "graph" if graph else "streams"
+        rec[key + "_fwd_us"] = _event_loop_us(lambda i: m.forward(xin, mid), 10, stream)
+        rec[key + "_inv_us"] = _event_loop_us(lambda i: m.inverse(mid, back), 10, stream)
+        rec["groups"] = m.groups
+        rec["elements"] = m.total
+        m.close()
+    rec["fwd_frac"] = 8.0 * rec["elements"] / (rec["graph_fwd_us"] * 1e-6) / 1e9 / peak
+    out["batched"] = rec
+    torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_init("nccl")
@@ -406,6 +473,7 @@ def run_ours(args):
     serve = None
     if not args.no_serve:
         serve = run_serving(args, dev)
+    configs = None if args.no_configs else run_configs(dev, measured_peaks()[0])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -434,6 +502,7 @@ def run_ours(args):
             "kernels": kernels,
             "kernel_family": plan.family,
             "serve": serve,
+            "configs": configs,
             "e2e": {"value": e2e_us, "unit": UNIT, "h2d_bytes_per_step": 4 * n1 * n2,
                     "d2h_bytes_per_step": 4 * n1 * n2},
             "gpu_launches": args.steps * 2 * launches,

@@ -155,6 +155,70 @@ gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan);
 gbdct_status gbdct_plan_destroy(gbdct_plan_t plan);
 
 /*
+ * As gbdct_plan_create_batched with the kernel family named by `family`
+ * ("seq", "pair", "r64", "fs", "fsp" or "fs2"; every family computes the same
+ * transform).  Errors: INVALID_ARG (NULL or unknown name, and the checks of
+ * gbdct_plan_create_batched), UNSUPPORTED when that family does not support
+ * the shape, OOM, CUDA.  For a 3D plan the family applies to its 2D slices.
+ */
+gbdct_status gbdct_plan_create_family(gbdct_plan_t* out, int ndim, const int64_t* dims, int64_t batch, int kind,
+                                      int dtype, const char* family);
+
+/*
+ * Autotuned plan: times one forward + inverse (inverse only for the
+ * inverse-only kinds) of every kernel family that supports the shape and batch,
+ * on scratch buffers it allocates and frees, with CUDA events on a private
+ * stream, and returns the plan of the fastest.  The choice is cached for the
+ * process and, when the environment variable GBDCT_TUNE_CACHE names a file,
+ * appended to that file ("key family microseconds" lines) and read back by
+ * later processes, which then create the plan without timing.  family_out
+ * (optional, family_cap bytes) receives the chosen family's name.
+ * Synchronises the device.  Errors as gbdct_plan_create_batched.
+ */
+gbdct_status gbdct_plan_create_tuned(gbdct_plan_t* out, int ndim, const int64_t* dims, int64_t batch, int kind,
+                                     int dtype, char* family_out, size_t family_cap);
+
+/*
+ * Uneven-size batches of 2D transforms (the batch parallelism of Section IV:
+ * independent transforms are independent units of work).  The executor groups
+ * the `count` transforms by shape into batched plans and defines a packed
+ * layout: transform i starts gbdct_multi_offset(m, i) floats into a buffer of
+ * gbdct_multi_total_elems(m) floats (groups back to back, largest shapes
+ * first; every offset is a multiple of 4 floats).  One exec transforms every
+ * transform of the packed input into the same place of the packed output.
+ *   shapes  count (N1, N2) pairs, each side a power of two in [2, 16384].
+ *   kind    a gbdct_kind (the inverse-only kinds reject forward execs).
+ *   flags   GBDCT_MULTI_GRAPH: the first exec for a given (in, out,
+ *           direction) captures the whole fork/join of the groups as one CUDA
+ *           graph, later execs with the same pointers replay it (one launch);
+ *           up to 8 graphs are kept.  Capture needs the calling thread to have
+ *           no other capture in progress.
+ *           GBDCT_MULTI_TUNE: each group's plan comes from
+ *           gbdct_plan_create_tuned (plan creation takes longer).
+ * Exec is asynchronous on `stream`: the groups run on the executor's own
+ * streams between a fork and a join on `stream`.  An executor may be used by
+ * one stream at a time.  Errors: INVALID_ARG (NULL, count < 1, dims <= 0,
+ * unknown kind or flags, misaligned pointers), UNSUPPORTED (a shape outside the
+ * limits; forward of an inverse-only kind), OOM, CUDA.
+ */
+typedef struct gbdct_multi_s* gbdct_multi_t;
+#define GBDCT_MULTI_GRAPH 1
+#define GBDCT_MULTI_TUNE 2
+gbdct_status gbdct_multi_create(gbdct_multi_t* out, int count, const int64_t* shapes, int kind, int flags);
+/* Offset (floats) of transform `index` in the packed buffers; -1 if out of range or NULL. */
+int64_t gbdct_multi_offset(gbdct_multi_t m, int index);
+/* Floats in a packed buffer (0 for NULL). */
+int64_t gbdct_multi_total_elems(gbdct_multi_t m);
+/* Number of shape groups (batched plans); 0 for NULL. */
+int gbdct_multi_group_count(gbdct_multi_t m);
+/* Kernel family of group `group`'s plan ("" if out of range). */
+const char* gbdct_multi_group_family(gbdct_multi_t m, int group);
+/* Forward (inverse = 0) or inverse transform of every transform in the packed buffers. */
+gbdct_status gbdct_multi_exec(gbdct_multi_t m, int inverse, const void* in, void* out, void* stream);
+/* Releases the executor, its plans, streams and graphs (NULL accepted). */
+gbdct_status gbdct_multi_destroy(gbdct_multi_t m);
+
+/*
  * Spectral Neumann Poisson solve of Section V-B, Algorithm 4 (the electrostatic
  * step of analytical placement).  For a density map rho (N1 x N2 float32):
  *   a    = DCT-II(rho)                                   (forward, as above)

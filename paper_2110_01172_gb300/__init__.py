@@ -9,5 +9,5 @@ synthetic workloads.
 
 __version__ = "0.1.0"
 
-from .binding import (Plan, dct2, idct2, dct3, idct3, dst2, idst2, idct_idxst, idxst_idct,  # noqa: F401,E402
+from .binding import (Plan, MultiPlan, dct2, idct2, dct3, idct3, dst2, idst2, idct_idxst, idxst_idct,  # noqa: F401,E402
                       PoissonSolver, load, GbdctError)

@@ -24,6 +24,8 @@ ERR_TIMEOUT = 5
 
 KINDS = {"dct2": 0, "dst2": 1, "idct_idxst": 2, "idxst_idct": 3}
 F32 = 0
+GRAPH = 1   # GBDCT_MULTI_GRAPH
+TUNE = 2    # GBDCT_MULTI_TUNE
 
 HEADER = os.path.join(_build.ROOT, "include", "gbdct.h")
 
@@ -83,6 +85,21 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_poisson_destroy": (ctypes.c_int, [plan_p]),
             "gbdct_dct2d_forward_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                            ctypes.c_int64, ctypes.c_void_p]),
+            "gbdct_plan_create_family": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int, c_i64p,
+                                                        ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.c_char_p]),
+            "gbdct_plan_create_tuned": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int, c_i64p,
+                                                       ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                                       ctypes.c_char_p, ctypes.c_size_t]),
+            "gbdct_multi_create": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int, c_i64p, ctypes.c_int,
+                                                  ctypes.c_int]),
+            "gbdct_multi_offset": (ctypes.c_int64, [plan_p, ctypes.c_int]),
+            "gbdct_multi_total_elems": (ctypes.c_int64, [plan_p]),
+            "gbdct_multi_group_count": (ctypes.c_int, [plan_p]),
+            "gbdct_multi_group_family": (ctypes.c_char_p, [plan_p, ctypes.c_int]),
+            "gbdct_multi_exec": (ctypes.c_int, [plan_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
+            "gbdct_multi_destroy": (ctypes.c_int, [plan_p]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -123,7 +140,10 @@ class Plan:
     to back; kind: "dct2" (forward DCT-II, inverse = exact inverse).
     """
 
-    def __init__(self, shape, kind: str = "dct2", batch: int = 1, device=None):
+    def __init__(self, shape, kind: str = "dct2", batch: int = 1, device=None, family: str | None = None,
+                 tuned: bool = False):
+        """family: force a kernel family ("seq", "pair", "r64", "fs", "fsp", "fs2");
+        tuned: pick the fastest family by timing (gbdct_plan_create_tuned)."""
         torch = _torch()
         lib = load()
         if kind not in KINDS:
@@ -135,9 +155,14 @@ class Plan:
                                    torch.device(device).index or 0)
         dims = (ctypes.c_int64 * len(self.shape))(*self.shape)
         handle = ctypes.c_void_p()
+        args = (ctypes.byref(handle), len(self.shape), dims, self.batch, KINDS[kind], F32)
         with torch.cuda.device(self.device):
-            _check(lib.gbdct_plan_create_batched(ctypes.byref(handle), len(self.shape), dims,
-                                                 self.batch, KINDS[kind], F32), "gbdct_plan_create")
+            if family is not None:
+                _check(lib.gbdct_plan_create_family(*args, family.encode()), "gbdct_plan_create_family")
+            elif tuned:
+                _check(lib.gbdct_plan_create_tuned(*args, None, 0), "gbdct_plan_create_tuned")
+            else:
+                _check(lib.gbdct_plan_create_batched(*args), "gbdct_plan_create")
         self._h = handle
         self._lib = lib
 
@@ -208,6 +233,79 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.gbdct_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MultiPlan:
+    """Uneven-size batch of 2D transforms (gbdct_multi_*): groups by shape into
+    batched plans over one packed buffer; optionally replayed as a CUDA graph."""
+
+    def __init__(self, shapes, kind: str = "dct2", graph: bool = True, tuned: bool = False, device=None):
+        torch = _torch()
+        lib = load()
+        if kind not in KINDS:
+            raise ValueError(f"unknown kind {kind!r}")
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        if not self.shapes or any(len(sh) != 2 for sh in self.shapes):
+            raise ValueError("expected a non-empty list of (N1, N2) shapes")
+        self.kind = kind
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        flat = (ctypes.c_int64 * (2 * len(self.shapes)))(*[v for sh in self.shapes for v in sh])
+        flags = (GRAPH if graph else 0) | (TUNE if tuned else 0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.gbdct_multi_create(ctypes.byref(h), len(self.shapes), flat, KINDS[kind], flags),
+                   "gbdct_multi_create")
+        self._h = h
+        self._lib = lib
+        self.offsets = [int(lib.gbdct_multi_offset(h, i)) for i in range(len(self.shapes))]
+        self.total = int(lib.gbdct_multi_total_elems(h))
+
+    @property
+    def groups(self) -> int:
+        return int(self._lib.gbdct_multi_group_count(self._h))
+
+    def group_families(self):
+        return [self._lib.gbdct_multi_group_family(self._h, g).decode() for g in range(self.groups)]
+
+    def pack(self, tensors, out=None):
+        """Copy a list of (N1, N2) tensors into one packed CUDA float32 buffer."""
+        torch = _torch()
+        buf = torch.empty(self.total, dtype=torch.float32, device=self.device) if out is None else out
+        for t, off, sh in zip(tensors, self.offsets, self.shapes):
+            buf[off:off + sh[0] * sh[1]].view(sh).copy_(t)
+        return buf
+
+    def unpack(self, buf):
+        """Views of the transforms inside a packed buffer."""
+        return [buf[off:off + sh[0] * sh[1]].view(sh) for off, sh in zip(self.offsets, self.shapes)]
+
+    def _exec(self, inverse, x, out, stream):
+        torch = _torch()
+        if x.dtype != torch.float32 or not x.is_cuda or x.numel() != self.total or not x.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA float32 buffer of {self.total} values")
+        out = torch.empty_like(x) if out is None else out
+        _check(self._lib.gbdct_multi_exec(self._h, int(inverse), ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, x.device)),
+               "gbdct_multi_exec")
+        return out
+
+    def forward(self, x, out=None, stream=None):
+        return self._exec(False, x, out, stream)
+
+    def inverse(self, x, out=None, stream=None):
+        return self._exec(True, x, out, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gbdct_multi_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -194,7 +194,11 @@ static gbdct_status run_plan(gbdct_plan_t p, bool inverse, int step, const void*
   return exec2d(p, in, out, reinterpret_cast<void*>(s), inverse, step);
 }
 
-static gbdct_status create_3d(gbdct_plan_t* out, const int64_t* dims, int64_t batch, int kind, int dtype) {
+static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims, int64_t batch, int kind,
+                                int dtype, const char* force);
+
+static gbdct_status create_3d(gbdct_plan_t* out, const int64_t* dims, int64_t batch, int kind, int dtype,
+                              const char* force) {
   if (kind != GBDCT_DCT2) return GBDCT_ERR_UNSUPPORTED;
   for (int i = 0; i < 3; ++i)
     if (!is_pow2(dims[i])) return GBDCT_ERR_UNSUPPORTED;
@@ -212,7 +216,7 @@ static gbdct_status create_3d(gbdct_plan_t* out, const int64_t* dims, int64_t ba
     delete p;
     return GBDCT_ERR_CUDA;
   }
-  gbdct_status st = gbdct_plan_create_batched(&p->inner, 2, dims + 1, batch * dims[0], GBDCT_DCT2, dtype);
+  gbdct_status st = create_impl(&p->inner, 2, dims + 1, batch * dims[0], GBDCT_DCT2, dtype, force);
   if (st != GBDCT_OK) {
     free_plan(p);
     return st;
@@ -288,13 +292,32 @@ const char* gbdct_version(void) { return "gbdct 0.1.0 sm_103a"; }
 
 gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_t* dims,
                                        int64_t batch, int kind, int dtype) {
+  return create_impl(out, ndim, dims, batch, kind, dtype, nullptr);
+}
+
+gbdct_status gbdct_plan_create_family(gbdct_plan_t* out, int ndim, const int64_t* dims, int64_t batch, int kind,
+                                      int dtype, const char* family) {
+  if (!family) return GBDCT_ERR_INVALID_ARG;
+  return create_impl(out, ndim, dims, batch, kind, dtype, family);
+}
+
+}  // extern "C"
+
+// force: a family name that must be used (UNSUPPORTED if it does not support
+// the shape), or NULL for the default choice (GBDCT_KERNEL_FAMILY may override
+// it when the named family supports the shape).
+static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims, int64_t batch, int kind,
+                                int dtype, const char* force) {
   if (!out || !dims || batch < 1) return GBDCT_ERR_INVALID_ARG;
   if (ndim < 1 || ndim > 3) return GBDCT_ERR_INVALID_ARG;
   for (int i = 0; i < ndim; ++i)
     if (dims[i] <= 0) return GBDCT_ERR_INVALID_ARG;
   if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
   if (dtype != GBDCT_F32) return GBDCT_ERR_UNSUPPORTED;
-  if (ndim == 3) return create_3d(out, dims, batch, kind, dtype);
+  if (force && strcmp(force, "seq") && strcmp(force, "pair") && strcmp(force, "r64") && strcmp(force, "fs") &&
+      strcmp(force, "fsp") && strcmp(force, "fs2"))
+    return GBDCT_ERR_INVALID_ARG;
+  if (ndim == 3) return create_3d(out, dims, batch, kind, dtype, force);
   if (ndim != 2) return GBDCT_ERR_UNSUPPORTED;
   for (int i = 0; i < ndim; ++i) {
     if (!is_pow2(dims[i])) return GBDCT_ERR_UNSUPPORTED;
@@ -334,13 +357,20 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   p->family = fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
   // GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp|fs2 forces a family when it supports the shape
   // (used to test and compare every kernel family on the same inputs).
-  if (const char* f = getenv("GBDCT_KERNEL_FAMILY")) {
-    if (!strcmp(f, "seq")) p->family = FAM_SEQ;
-    else if (!strcmp(f, "pair") && pair) p->family = FAM_PAIR;
-    else if (!strcmp(f, "r64") && r64) p->family = FAM_R64;
-    else if (!strcmp(f, "fs") && fs) p->family = FAM_FS;
-    else if (!strcmp(f, "fsp") && fsp) p->family = FAM_FSP;
-    else if (!strcmp(f, "fs2") && fs2) p->family = FAM_FS2;
+  if (const char* f = force ? force : getenv("GBDCT_KERNEL_FAMILY")) {
+    const int before = p->family;
+    int chosen = -1;
+    if (!strcmp(f, "seq")) chosen = FAM_SEQ;
+    else if (!strcmp(f, "pair") && pair) chosen = FAM_PAIR;
+    else if (!strcmp(f, "r64") && r64) chosen = FAM_R64;
+    else if (!strcmp(f, "fs") && fs) chosen = FAM_FS;
+    else if (!strcmp(f, "fsp") && fsp) chosen = FAM_FSP;
+    else if (!strcmp(f, "fs2") && fs2) chosen = FAM_FS2;
+    if (chosen < 0 && force) {
+      delete p;
+      return GBDCT_ERR_UNSUPPORTED;
+    }
+    p->family = chosen < 0 ? before : chosen;
   }
   const bool four_step = p->family == FAM_FS || p->family == FAM_FSP || p->family == FAM_FS2;
   p->pmax = (p->family == FAM_R64 || p->family == FAM_FS || p->family == FAM_FSP) ? gbdct::r64::PMAX : 16;
@@ -452,6 +482,8 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
   *out = p;
   return GBDCT_OK;
 }
+
+extern "C" {
 
 gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims, int kind,
                                int dtype) {

@@ -78,3 +78,29 @@ def test_null_handles(lib):
     h = ctypes.c_void_p()
     assert lib.gbdct_plan_create(ctypes.byref(h), 2, None, 0, 0) == binding.ERR_INVALID_ARG
     assert lib.gbdct_plan_create(None, 2, (ctypes.c_int64 * 2)(8, 8), 0, 0) == binding.ERR_INVALID_ARG
+
+
+def test_multi_and_family_rejections_before_touching_the_gpu(lib):
+    h = ctypes.c_void_p()
+    shapes = (ctypes.c_int64 * 4)(64, 64, 128, 64)
+    assert lib.gbdct_multi_create(ctypes.byref(h), 0, shapes, 0, 0) == binding.ERR_INVALID_ARG      # count
+    assert lib.gbdct_multi_create(ctypes.byref(h), 2, None, 0, 0) == binding.ERR_INVALID_ARG        # shapes
+    assert lib.gbdct_multi_create(None, 2, shapes, 0, 0) == binding.ERR_INVALID_ARG                 # out
+    assert lib.gbdct_multi_create(ctypes.byref(h), 2, shapes, 7, 0) == binding.ERR_INVALID_ARG      # kind
+    assert lib.gbdct_multi_create(ctypes.byref(h), 2, shapes, 0, 8) == binding.ERR_INVALID_ARG      # flags
+    bad = (ctypes.c_int64 * 4)(64, 64, 96, 64)
+    assert lib.gbdct_multi_create(ctypes.byref(h), 2, bad, 0, 0) == binding.ERR_UNSUPPORTED        # not pow2
+    neg = (ctypes.c_int64 * 2)(64, 0)
+    assert lib.gbdct_multi_create(ctypes.byref(h), 1, neg, 0, 0) == binding.ERR_INVALID_ARG
+    assert not h.value
+    assert lib.gbdct_multi_offset(None, 0) == -1
+    assert lib.gbdct_multi_total_elems(None) == 0
+    assert lib.gbdct_multi_group_count(None) == 0
+    assert lib.gbdct_multi_group_family(None, 0) == b""
+    assert lib.gbdct_multi_exec(None, 0, None, None, None) == binding.ERR_INVALID_ARG
+    assert lib.gbdct_multi_destroy(None) == binding.OK
+    dims = (ctypes.c_int64 * 2)(256, 256)
+    assert lib.gbdct_plan_create_family(ctypes.byref(h), 2, dims, 1, 0, 0, b"fft") == binding.ERR_INVALID_ARG
+    assert lib.gbdct_plan_create_family(ctypes.byref(h), 2, dims, 1, 0, 0, None) == binding.ERR_INVALID_ARG
+    assert lib.gbdct_plan_create_tuned(ctypes.byref(h), 2, dims, 0, 0, 0, None, 0) == binding.ERR_INVALID_ARG
+    assert not h.value
