@@ -16,6 +16,18 @@
 // Workspace layout as in dct2d_fs_kernels.cuh: N1 rows of N2/2 complex, row
 // k1 of the column spectrum at physical row (k1 % B) * A + k1 / B.
 // Supported: N1 in {256, ..., 4096}, N2 in {256, ..., 16384}.
+//
+// The other kinds are index/sign maps around the DCT-II (Section V-B, Eq.
+// idxst; DST-II per axis), folded into the first loads and last stores
+// (a.vkind):
+//   DST-II forward   x(n1,n2) (-1)^(n1+n2) in C1's loads; output (k1,k2) stored
+//                    at (N1-1-k1, N2-1-k2) by the row pass
+//   DST-II inverse   input read at (N1-1-k1, N2-1-k2) by the row pass's staging;
+//                    (-1)^(n1+n2) in C1''s stores
+//   IDCT_IDXST       input column k2 taken from column N2-k2 (column 0 zero):
+//                    the preprocess swaps its reads k2 <-> N2-k2; (-1)^n2 in C1'
+//   IDXST_IDCT       input row k1 taken from row N1-k1 (row 0 zero): the row
+//                    pass swaps its two rows; (-1)^n1 in C1''s stores
 #pragma once
 
 #include "dct2d_kernels.cuh"
@@ -111,7 +123,14 @@ k_fs2_col(Dct2dArgs a) {
     const float2* src;
     if constexpr (KIND == 0) {
       const float* xin = a.in + (long long)blockIdx.z * a.in_bstride;
-      src = reinterpret_cast<const float2*>(xin + (long long)reorder_src(r + G::A * i, N1) * N2) + col;
+      const int row = reorder_src(r + G::A * i, N1);
+      src = reinterpret_cast<const float2*>(xin + (long long)row * N2) + col;
+      x[j] = *src;
+      if (a.vkind == 1) {  // DST-II: (-1)^(n1 + n2) on columns 2 col, 2 col + 1
+        const float sr = (row & 1) ? -1.f : 1.f;
+        x[j] = make_float2(sr * x[j].x, -sr * x[j].y);
+      }
+      continue;
     } else if constexpr (KIND == 3) {
       src = W + (long long)(i * G::A + r) * half + col;
     } else {
@@ -136,7 +155,13 @@ k_fs2_col(Dct2dArgs a) {
         W[(long long)(r * G::A + o) * half + col] = y;
       } else {
         float* xo = a.out + (long long)blockIdx.z * a.out_bstride;
-        *(reinterpret_cast<float2*>(xo + (long long)reorder_src(r + G::A * o, N1) * N2) + col) = y;
+        const int row = reorder_src(r + G::A * o, N1);
+        if (a.vkind) {  // output signs: (-1)^(n1+n2) DST-II, (-1)^n2 IDCT_IDXST, (-1)^n1 IDXST_IDCT
+          const float sr = (a.vkind != 2 && (row & 1)) ? -1.f : 1.f;
+          const float sc = (a.vkind != 3) ? -sr : sr;
+          y = make_float2(sr * y.x, sc * y.y);
+        }
+        *(reinterpret_cast<float2*>(xo + (long long)row * N2) + col) = y;
       }
     }
 }
@@ -159,8 +184,11 @@ struct RowGeom {
 
 // Copies two rows of L floats (row0 -> sf[0, L), row1 -> sf[L, 2L)) into shared
 // memory with 16-byte loads; TPS threads of one item, L/16 ... L/2 float4 each.
+// rev: each row is stored reversed (sf[k] = row[L-1-k]); row0 == nullptr
+// stages zeros for the first row.
 template <int L, int TPS>
-__device__ __forceinline__ void stage_two_rows(float* sf, const float* row0, const float* row1, int g) {
+__device__ __forceinline__ void stage_two_rows(float* sf, const float* row0, const float* row1, int g,
+                                               bool rev = false) {
   const float4* a4 = reinterpret_cast<const float4*>(row0);
   const float4* b4 = reinterpret_cast<const float4*>(row1);
   float4* s4 = reinterpret_cast<float4*>(sf);
@@ -168,8 +196,13 @@ __device__ __forceinline__ void stage_two_rows(float* sf, const float* row0, con
   float4 t[2 * Q / TPS];
 #pragma unroll
   for (int j = 0; j < Q / TPS; ++j) {
-    t[j] = a4[g + j * TPS];
-    t[Q / TPS + j] = b4[g + j * TPS];
+    const int q = rev ? Q - 1 - (g + j * TPS) : g + j * TPS;
+    t[j] = a4 ? a4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    t[Q / TPS + j] = b4[q];
+    if (rev) {
+      t[j] = make_float4(t[j].w, t[j].z, t[j].y, t[j].x);
+      t[Q / TPS + j] = make_float4(t[Q / TPS + j].w, t[Q / TPS + j].z, t[Q / TPS + j].y, t[Q / TPS + j].x);
+    }
   }
 #pragma unroll
   for (int j = 0; j < Q / TPS; ++j) {
@@ -220,8 +253,9 @@ k_fs2_fwd_rows(Dct2dArgs a) {
   fft_stages<L, 16, false>(s, g, a.tw2);
 
   const float2 av = __ldg(a.fa + k1);
-  float* row0 = y + (long long)k1 * L;
-  float* row1 = y + (long long)kmir * L;
+  const bool rev = a.vkind == 1;  // DST-II: output (k1, k2) goes to (N1-1-k1, N2-1-k2)
+  float* row0 = y + (long long)(rev ? N1 - 1 - k1 : k1) * L;
+  float* row1 = y + (long long)(rev ? N1 - 1 - kmir : kmir) * L;
   constexpr float RH = 0.70710678118654752f;
   for (int i = g; i < L / 8; i += R::TPS) {
     const int c = 4 * i;
@@ -276,10 +310,17 @@ k_fs2_fwd_rows(Dct2dArgs a) {
       }
       if (e) { r0[0] = o0; r1[0] = o1; } else { q0[0] = o0; q1[0] = o1; }
     }
-    *reinterpret_cast<float4*>(row0 + c) = make_float4(q0[0], q0[1], q0[2], q0[3]);
-    *reinterpret_cast<float4*>(row1 + c) = make_float4(q1[0], q1[1], q1[2], q1[3]);
-    *reinterpret_cast<float4*>(row0 + L - c - 4) = make_float4(r0[0], r0[1], r0[2], r0[3]);
-    *reinterpret_cast<float4*>(row1 + L - c - 4) = make_float4(r1[0], r1[1], r1[2], r1[3]);
+    if (!rev) {
+      *reinterpret_cast<float4*>(row0 + c) = make_float4(q0[0], q0[1], q0[2], q0[3]);
+      *reinterpret_cast<float4*>(row1 + c) = make_float4(q1[0], q1[1], q1[2], q1[3]);
+      *reinterpret_cast<float4*>(row0 + L - c - 4) = make_float4(r0[0], r0[1], r0[2], r0[3]);
+      *reinterpret_cast<float4*>(row1 + L - c - 4) = make_float4(r1[0], r1[1], r1[2], r1[3]);
+    } else {
+      *reinterpret_cast<float4*>(row0 + L - c - 4) = make_float4(q0[3], q0[2], q0[1], q0[0]);
+      *reinterpret_cast<float4*>(row1 + L - c - 4) = make_float4(q1[3], q1[2], q1[1], q1[0]);
+      *reinterpret_cast<float4*>(row0 + c) = make_float4(r0[3], r0[2], r0[1], r0[0]);
+      *reinterpret_cast<float4*>(row1 + c) = make_float4(r1[3], r1[2], r1[1], r1[0]);
+    }
   }
 }
 
@@ -302,6 +343,14 @@ k_fs2_inv_rows(Dct2dArgs a) {
   const float* C = a.in + (long long)blockIdx.z * a.in_bstride;
   const float* ca = C + (long long)k1 * L;
   const float* cb = C + (long long)kmir * L;
+  if (a.vkind == 1) {  // DST-II inverse: input (k1, k2) read at (N1-1-k1, N2-1-k2)
+    ca = C + (long long)(N1 - 1 - k1) * L;
+    cb = C + (long long)(N1 - 1 - kmir) * L;
+  } else if (a.vkind == 3) {  // IDXST_IDCT: row k1 from row N1-k1, row 0 zero
+    const float* t = ca;
+    ca = packed ? nullptr : cb;
+    cb = packed ? cb : t;
+  }
   float2* Zw = a.work + (long long)blockIdx.z * a.work_bstride;
   const float2 ia = __ldg(a.ia + k1);
   const float2 ih = __ldg(a.ia + N1 / 2);
@@ -309,16 +358,21 @@ k_fs2_inv_rows(Dct2dArgs a) {
   // rows k1 and kmir of C into the item's FFT buffer (raw layout), then the
   // four-read preprocess reads them from there
   const float* sf = reinterpret_cast<const float*>(s);
-  stage_two_rows<L, R::TPS>(reinterpret_cast<float*>(s), ca, cb, g);
+  stage_two_rows<L, R::TPS>(reinterpret_cast<float*>(s), ca, cb, g, a.vkind == 1);
   __syncthreads();
+  // IDCT_IDXST: input column k2 from column N2-k2 (column 0 zero), i.e. the
+  // reads at k2 and N2-k2 trade places
+  const bool swapc = a.vkind == 2;
   float2 v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const int k2 = g + j * R::TPS;
     const int km = (L - k2) & (L - 1);
-    const float c1 = sf[k2], c3 = sf[L + k2];
-    const float c4 = k2 ? sf[km] : 0.f;
-    const float c2 = k2 ? sf[L + km] : 0.f;
+    const int ka = swapc ? km : k2, kb = swapc ? k2 : km;
+    const float c1 = (swapc && !k2) ? 0.f : sf[ka];
+    const float c3 = (swapc && !k2) ? 0.f : sf[L + ka];
+    const float c4 = k2 ? sf[kb] : 0.f;
+    const float c2 = k2 ? sf[L + kb] : 0.f;
     const float2 bk = __ldg(a.ib + k2);
     if (packed) {
       const float2 v0 = cmul(cmul(make_float2(c1, -c4), bk), ia);

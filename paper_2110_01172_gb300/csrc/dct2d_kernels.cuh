@@ -57,6 +57,8 @@ struct Dct2dArgs {
   int* err;           // device error word: set to 1 by a bounded wait that gave up
   int step_filter;    // host side only: -1 runs every launch, k runs launch k alone
   int fsA, fsB;       // four-step split N1 = A * B (four-step families)
+  int vkind;          // kind whose index/sign maps the fs2 kernels fold into their
+                      // loads and stores (0: DCT-II, no map; see dct2d_fs2_kernels.cuh)
 };
 
 template <int L>

@@ -399,7 +399,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
 
   p->work_bytes = (size_t)batch * (size_t)(n1 / 2) * (size_t)n2 * sizeof(float2);
   e = cudaMalloc(&p->work, p->work_bytes);
-  if (e == cudaSuccess && kind != GBDCT_DCT2)
+  // staging array for the map kernels of the other kinds (fs2 folds the maps in)
+  if (e == cudaSuccess && kind != GBDCT_DCT2 && p->family != FAM_FS2)
     e = cudaMalloc(&p->tmp, (size_t)batch * (size_t)n1 * (size_t)n2 * sizeof(float));
   if (e != cudaSuccess) {
     free_plan(p);
@@ -445,6 +446,7 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   a.step_filter = -1;
   a.fsA = fsA;
   a.fsB = fsB;
+  a.vkind = p->family == FAM_FS2 ? kind : 0;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 
@@ -513,6 +515,8 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (p->ndim == 3) return exec3d(p, in, out, s, inverse, step);
   if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse, step);
+  if (!inverse && (p->kind == GBDCT_IDCT_IDXST || p->kind == GBDCT_IDXST_IDCT)) return GBDCT_ERR_UNSUPPORTED;
+  if (p->family == FAM_FS2) return exec_core(p, in, out, s, inverse, step);  // maps folded in (vkind)
   MapSpec pre{}, post{};
   if (p->kind == GBDCT_DST2) {
     if (!inverse) {
@@ -632,7 +636,7 @@ const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step) {
                                 "column step C1' (DFT_B + inverse reorder)"};
   const bool three = core_launches(plan) == 3;
   int k = step;
-  if (plan->kind != GBDCT_DCT2) {
+  if (plan->kind != GBDCT_DCT2 && plan->family != FAM_FS2) {
     if (k == 0) return "index/sign map (pre)";
     if (k == gbdct_plan_launches_per_exec(plan) - 1) return "index/sign map (post)";
     k -= 1;
@@ -647,7 +651,7 @@ int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (!plan) return 0;
   if (plan->ndim == 3) return gbdct_plan_launches_per_exec(plan->inner) + 1;
   const int core = core_launches(plan);
-  return plan->kind == GBDCT_DCT2 ? core : core + 2;
+  return (plan->kind == GBDCT_DCT2 || plan->family == FAM_FS2) ? core : core + 2;
 }
 
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {

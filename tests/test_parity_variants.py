@@ -63,3 +63,56 @@ def test_idxst_kinds(kind, shape):
             assert abs(yh[i, j] - ref) <= MAX_ABS * np.abs(yh).max()
     buf = torch.zeros(shape, device="cuda")
     assert plan.forward_ptr(buf.data_ptr(), buf.data_ptr()) == binding.ERR_UNSUPPORTED
+
+
+FOLD_SHAPES = [(256, 256), (512, 256), (256, 1024), (1024, 512), (256, 16384)]
+
+
+@pytest.mark.parametrize("family", ["fs2", "pair"])
+@pytest.mark.parametrize("shape", FOLD_SHAPES)
+def test_kinds_folded_and_mapped_paths(family, shape):
+    """fs2 folds each kind's index/sign maps into its first loads and last
+    stores; pair runs the map kernels around the DCT-II.  Both against the
+    oracle, for every kind, forward and inverse where defined."""
+    from paper_2110_01172_gb300 import Plan
+    if family == "pair" and max(shape) > 8192:
+        pytest.skip("pair supports sides up to 8192")
+    x = inputs.uniform(shape, seed=44)
+    xd = torch.from_numpy(x).cuda()
+    p = Plan(shape, "dst2", family=family)
+    assert p.family == family
+    assert p.launches_per_exec == (3 if family == "fs2" else 4)
+    S = p.forward(xd)
+    back = p.inverse(S)
+    torch.cuda.synchronize()
+    Sh = S.cpu().numpy()
+    check(Sh, oracle.dst2_2d(x))
+    check(back.cpu().numpy(), oracle.idst2_2d(Sh))
+    for kind, ref in (("idct_idxst", oracle.idct_idxst), ("idxst_idct", oracle.idxst_idct)):
+        q = Plan(shape, kind, family=family)
+        y = q.inverse(xd)
+        torch.cuda.synchronize()
+        check(y.cpu().numpy(), ref(x))
+
+
+def test_folded_kinds_batched_and_in_place():
+    from paper_2110_01172_gb300 import Plan
+    shape = (512, 1024)
+    xs = np.stack([inputs.uniform(shape, seed=45 + i) for i in range(3)])
+    p = Plan(shape, "dst2", batch=3)
+    assert p.family == "fs2"
+    xd = torch.from_numpy(xs).cuda()
+    S = p.forward(xd)
+    torch.cuda.synchronize()
+    for i in range(3):
+        check(S[i].cpu().numpy(), oracle.dst2_2d(xs[i]))
+    p.inverse(S, out=S)
+    torch.cuda.synchronize()
+    for i in range(3):
+        check(S[i].cpu().numpy(), xs[i])
+    q = Plan(shape, "idxst_idct", batch=3)
+    y = xd.clone()
+    q.inverse(y, out=y)
+    torch.cuda.synchronize()
+    for i in range(3):
+        check(y[i].cpu().numpy(), oracle.idxst_idct(xs[i]))
