@@ -49,15 +49,15 @@ FALLBACK_HBM_GBS = 6800.0
 # from the ncu capture summarised in profiles/, valid only for the kernel
 # sources with this digest (otherwise reported as null).
 TRAFFIC = {
-    "sources_sha256": "ff18c643529afad45ad92d970888359599607c7633ae1ea4b4a8782007f499ff",
+    "sources_sha256": "39110cbe20d6865507c9cddf4fa0666816212b952b5a08d76274d44b5a768e73",
     "family": "fs2",
     "bytes_per_launch": {   # profiles/fs2_kernels_4096_ncu.md (cold L2 under ncu)
-        "forward column step C1 (reorder + DFT_B + twiddle)": 67163648 + 17660672,
-        "forward column step C2 (DFT_A)": 67122432 + 6854144,
-        "forward row pass (split + row FFT + postprocess)": 67222528 + 17004032,
-        "inverse row pass (preprocess + row IFFT + pairing)": 67224576 + 15966208,
-        "inverse column step C2' (DFT_A + twiddle)": 67156736 + 6844672,
-        "inverse column step C1' (DFT_B + inverse reorder)": 67127040 + 17150720,
+        "forward column step C1 (reorder + DFT_B + twiddle)": 67165440 + 17367040,
+        "forward column step C2 (DFT_A)": 67122432 + 6613760,
+        "forward row pass (split + row FFT + postprocess)": 67231488 + 17267456,
+        "inverse row pass (preprocess + row IFFT + pairing)": 67238144 + 16097792,
+        "inverse column step C2' (DFT_A + twiddle)": 67156992 + 6772224,
+        "inverse column step C1' (DFT_B + inverse reorder)": 67128576 + 17273856,
     },
 }
 

@@ -32,6 +32,7 @@
 
 #include "dct2d_kernels.cuh"
 #include "fft_r64.cuh"
+#include "pipe.cuh"
 
 namespace gbdct {
 
@@ -167,10 +168,16 @@ k_fs2_col(Dct2dArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// Forward row pass (L = N2): split in the loads, row FFT, symmetric-pair
-// postprocess (Section III-B, Eqs. four-elements, s-t).  Item k1 in [0, N1/2):
-// row k1 >= 1 gives output rows k1 and N1-k1; item 0 is the packed pair
-// V1(0,.) + i V1(N1/2,.) and gives rows 0 and N1/2.
+// Row passes (L = N2).  Item k1 in [0, N1/2) owns the row pair (k1, N1-k1);
+// item 0 the packed pair (0, N1/2).  Forward: Hermitian split of the two
+// column-spectrum rows, row FFT, symmetric-pair postprocess (Section III-B,
+// Eqs. four-elements, s-t) -> output rows k1 and N1-k1.  Inverse: four-read
+// preprocess (Eq. 2d_idct_pre, conjugated twiddle, 1/(N1 N2) in the a-table),
+// row IFFT, column pairing Z_p(k1) = U(k1,p) + i U(k1,L-1-p) -> workspace.
+// Two variants share the arithmetic: one item group per CTA with the rows
+// staged by the threads (k_fs2_*_rows), and persistent CTAs that prefetch the
+// next item's rows with bulk copies while computing the current one
+// (k_fs2p_rows).
 // ----------------------------------------------------------------------------
 template <int L>
 struct RowGeom {
@@ -180,15 +187,54 @@ struct RowGeom {
   static constexpr int LP = pad_len<float2>(L);
   static constexpr size_t SMEM = (size_t)NI * LP * sizeof(float2);
   static constexpr int MINB = 1024 / THREADS;  // caps registers at 64 per thread
+  static constexpr size_t STAGE = (size_t)NI * 2 * L * sizeof(float);  // raw rows of the persistent variant
+  static constexpr size_t PSMEM = STAGE + SMEM + 16;                  // + mbarrier
+  // persistent CTAs per SM that shared memory allows (registers bounded to match)
+  static constexpr int PMINB_SMEM = (int)((227 * 1024) / PSMEM);
+  static constexpr int PMINB = PMINB_SMEM < 1 ? 1 : (PMINB_SMEM < MINB ? PMINB_SMEM : MINB);
 };
 
+__device__ __forceinline__ int row_mirror(int k1, int N1) { return k1 ? N1 - k1 : N1 / 2; }
+
+// The two source rows (L floats each) of item k1 of batch entry b.  Forward:
+// column-spectrum rows k1 and its mirror in the workspace (four-step physical
+// order).  Inverse: input rows with the kind's row map folded in: DST-II reads
+// rows N1-1-k1 and N1-1-kmir (columns reversed by inv_pre); IDXST_IDCT takes
+// row k1 from row N1-k1, so the two rows trade places and the packed item's
+// row 0 is zero (*ra = nullptr).
+template <int L, bool INV>
+__device__ __forceinline__ void row_sources(const Dct2dArgs& a, int b, int k1, const float** ra, const float** rb) {
+  const int N1 = a.n1;
+  const int kmir = row_mirror(k1, N1);
+  if constexpr (!INV) {
+    const float2* Zw = a.work + (long long)b * a.work_bstride;
+    *ra = reinterpret_cast<const float*>(Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2));
+    *rb = reinterpret_cast<const float*>(Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2));
+  } else {
+    const float* C = a.in + (long long)b * a.in_bstride;
+    int r0 = k1, r1 = kmir;
+    if (a.vkind == 1) {
+      r0 = N1 - 1 - k1;
+      r1 = N1 - 1 - kmir;
+    }
+    *ra = C + (long long)r0 * L;
+    *rb = C + (long long)r1 * L;
+    if (a.vkind == 3) {
+      if (k1) {
+        const float* t = *ra;
+        *ra = *rb;
+        *rb = t;
+      } else {
+        *ra = nullptr;
+      }
+    }
+  }
+}
+
 // Copies two rows of L floats (row0 -> sf[0, L), row1 -> sf[L, 2L)) into shared
-// memory with 16-byte loads; TPS threads of one item, L/16 ... L/2 float4 each.
-// rev: each row is stored reversed (sf[k] = row[L-1-k]); row0 == nullptr
-// stages zeros for the first row.
+// memory with 16-byte loads (TPS threads); a null row0 is left unwritten.
 template <int L, int TPS>
-__device__ __forceinline__ void stage_two_rows(float* sf, const float* row0, const float* row1, int g,
-                                               bool rev = false) {
+__device__ __forceinline__ void stage_two_rows(float* sf, const float* row0, const float* row1, int g) {
   const float4* a4 = reinterpret_cast<const float4*>(row0);
   const float4* b4 = reinterpret_cast<const float4*>(row1);
   float4* s4 = reinterpret_cast<float4*>(sf);
@@ -196,50 +242,27 @@ __device__ __forceinline__ void stage_two_rows(float* sf, const float* row0, con
   float4 t[2 * Q / TPS];
 #pragma unroll
   for (int j = 0; j < Q / TPS; ++j) {
-    const int q = rev ? Q - 1 - (g + j * TPS) : g + j * TPS;
-    t[j] = a4 ? a4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-    t[Q / TPS + j] = b4[q];
-    if (rev) {
-      t[j] = make_float4(t[j].w, t[j].z, t[j].y, t[j].x);
-      t[Q / TPS + j] = make_float4(t[Q / TPS + j].w, t[Q / TPS + j].z, t[Q / TPS + j].y, t[Q / TPS + j].x);
-    }
+    if (a4) t[j] = a4[g + j * TPS];
+    t[Q / TPS + j] = b4[g + j * TPS];
   }
 #pragma unroll
   for (int j = 0; j < Q / TPS; ++j) {
-    s4[g + j * TPS] = t[j];
+    if (a4) s4[g + j * TPS] = t[j];
     s4[Q + g + j * TPS] = t[Q / TPS + j];
   }
 }
 
-template <int L>
-__global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::MINB)
-k_fs2_fwd_rows(Dct2dArgs a) {
-  const int N1 = a.n1;
-  using R = RowGeom<L>;
-  extern __shared__ float4 srw[];
-  const int li = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
-  float2* s = reinterpret_cast<float2*>(srw) + li * R::LP;
-  const int k1 = blockIdx.x * R::NI + li;
-  const bool packed = (k1 == 0);
-  const int kmir = packed ? N1 / 2 : N1 - k1;
-  const float2* Zw = a.work + (long long)blockIdx.z * a.work_bstride;
-  const float2* za_row = Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2);
-  const float2* zb_row = Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2);
-  float* y = a.out + (long long)blockIdx.z * a.out_bstride;
-
-  // both workspace rows (L/2 complex each) into the item's FFT buffer, raw
-  // layout, then the split reads them from there
-  stage_two_rows<L, R::TPS>(reinterpret_cast<float*>(s), reinterpret_cast<const float*>(za_row),
-                            reinterpret_cast<const float*>(zb_row), g);
-  __syncthreads();
-  float2 v[16];
+// Forward split: st holds rows za (L/2 complex) and zb (L/2 complex); returns
+// the thread's 16 points n2 = g + j TPS of the row to transform.
+template <int L, int TPS>
+__device__ __forceinline__ void fwd_split(const float2* st, bool packed, int g, float2* v) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const int n2 = g + j * R::TPS;
+    const int n2 = g + j * TPS;
     const bool lowhalf = n2 < L / 2;
     const int p = lowhalf ? n2 : L - 1 - n2;
-    const float2 za = s[p];
-    const float2 zb = s[L / 2 + p];
+    const float2 za = st[p];
+    const float2 zb = st[L / 2 + p];
     if (packed) {
       v[j] = lowhalf ? make_float2(za.x, zb.x) : make_float2(za.y, zb.y);
     } else {
@@ -247,17 +270,20 @@ k_fs2_fwd_rows(Dct2dArgs a) {
                      : make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
     }
   }
-  __syncthreads();
-  first_stage_regs<L, false>(v, s, g);
-  __syncthreads();
-  fft_stages<L, 16, false>(s, g, a.tw2);
+}
 
+// Forward postprocess from the row spectrum in s (padded layout) to output
+// rows k1 and kmir of y (DST-II: rows and columns reversed).
+template <int L, int TPS>
+__device__ __forceinline__ void fwd_post(const float2* s, const Dct2dArgs& a, float* y, int k1, int kmir,
+                                         bool packed, int g) {
+  const int N1 = a.n1;
   const float2 av = __ldg(a.fa + k1);
   const bool rev = a.vkind == 1;  // DST-II: output (k1, k2) goes to (N1-1-k1, N2-1-k2)
   float* row0 = y + (long long)(rev ? N1 - 1 - k1 : k1) * L;
   float* row1 = y + (long long)(rev ? N1 - 1 - kmir : kmir) * L;
   constexpr float RH = 0.70710678118654752f;
-  for (int i = g; i < L / 8; i += R::TPS) {
+  for (int i = g; i < L / 8; i += TPS) {
     const int c = 4 * i;
     float2 Yq[5], Ym[5];
 #pragma unroll
@@ -308,7 +334,13 @@ k_fs2_fwd_rows(Dct2dArgs a) {
         o0 = bt.x * u.x - bt.y * u.y;
         o1 = -(bt.x * w.y + bt.y * w.x);
       }
-      if (e) { r0[0] = o0; r1[0] = o1; } else { q0[0] = o0; q1[0] = o1; }
+      if (e) {
+        r0[0] = o0;
+        r1[0] = o1;
+      } else {
+        q0[0] = o0;
+        q1[0] = o1;
+      }
     }
     if (!rev) {
       *reinterpret_cast<float4*>(row0 + c) = make_float4(q0[0], q0[1], q0[2], q0[3]);
@@ -324,55 +356,32 @@ k_fs2_fwd_rows(Dct2dArgs a) {
   }
 }
 
-// ----------------------------------------------------------------------------
-// Inverse row pass (L = N2): four-read preprocess (Eq. 2d_idct_pre, conjugated
-// twiddle, 1/(N1 N2) in the a-table) + row IFFT + column pairing
-// Z_p(k1) = U(k1,p) + i U(k1,L-1-p), Z_p(N1-k1) = conj(...).
-// ----------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::MINB)
-k_fs2_inv_rows(Dct2dArgs a) {
-  const int N1 = a.n1;
-  using R = RowGeom<L>;
-  extern __shared__ float4 srw[];
-  const int li = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
-  float2* s = reinterpret_cast<float2*>(srw) + li * R::LP;
-  const int k1 = blockIdx.x * R::NI + li;
-  const bool packed = (k1 == 0);
-  const int kmir = packed ? N1 / 2 : N1 - k1;
-  const float* C = a.in + (long long)blockIdx.z * a.in_bstride;
-  const float* ca = C + (long long)k1 * L;
-  const float* cb = C + (long long)kmir * L;
-  if (a.vkind == 1) {  // DST-II inverse: input (k1, k2) read at (N1-1-k1, N2-1-k2)
-    ca = C + (long long)(N1 - 1 - k1) * L;
-    cb = C + (long long)(N1 - 1 - kmir) * L;
-  } else if (a.vkind == 3) {  // IDXST_IDCT: row k1 from row N1-k1, row 0 zero
-    const float* t = ca;
-    ca = packed ? nullptr : cb;
-    cb = packed ? cb : t;
-  }
-  float2* Zw = a.work + (long long)blockIdx.z * a.work_bstride;
-  const float2 ia = __ldg(a.ia + k1);
-  const float2 ih = __ldg(a.ia + N1 / 2);
-
-  // rows k1 and kmir of C into the item's FFT buffer (raw layout), then the
-  // four-read preprocess reads them from there
-  const float* sf = reinterpret_cast<const float*>(s);
-  stage_two_rows<L, R::TPS>(reinterpret_cast<float*>(s), ca, cb, g, a.vkind == 1);
-  __syncthreads();
-  // IDCT_IDXST: input column k2 from column N2-k2 (column 0 zero), i.e. the
-  // reads at k2 and N2-k2 trade places
-  const bool swapc = a.vkind == 2;
-  float2 v[16];
+// Inverse preprocess: sf holds the two source rows (L floats each, raw);
+// zero_a: the first row is zero (IDXST_IDCT, packed item).  DST-II reads the
+// columns reversed; IDCT_IDXST swaps the reads at k2 and N2-k2 (column 0 zero).
+template <int L, int TPS, bool MAPPED>
+__device__ __forceinline__ void inv_pre_loop(const float* sf, const Dct2dArgs& a, float2 ia, float2 ih, bool packed,
+                                             bool zero_a, int g, float2* v) {
+  const bool rev = MAPPED && a.vkind == 1, swapc = MAPPED && a.vkind == 2;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const int k2 = g + j * R::TPS;
+    const int k2 = g + j * TPS;
     const int km = (L - k2) & (L - 1);
-    const int ka = swapc ? km : k2, kb = swapc ? k2 : km;
-    const float c1 = (swapc && !k2) ? 0.f : sf[ka];
-    const float c3 = (swapc && !k2) ? 0.f : sf[L + ka];
-    const float c4 = k2 ? sf[kb] : 0.f;
-    const float c2 = k2 ? sf[L + kb] : 0.f;
+    float c1, c3, c4, c2;
+    if constexpr (!MAPPED) {
+      c1 = zero_a ? 0.f : sf[k2];
+      c3 = sf[L + k2];
+      c4 = (k2 && !zero_a) ? sf[km] : 0.f;
+      c2 = k2 ? sf[L + km] : 0.f;
+    } else {
+      const int ka = swapc ? km : k2, kb = swapc ? k2 : km;
+      const int pa = rev ? L - 1 - ka : ka, pb = rev ? L - 1 - kb : kb;
+      const bool z0 = swapc && !k2;
+      c1 = (zero_a || z0) ? 0.f : sf[pa];
+      c3 = z0 ? 0.f : sf[L + pa];
+      c4 = (k2 && !zero_a) ? sf[pb] : 0.f;
+      c2 = k2 ? sf[L + pb] : 0.f;
+    }
     const float2 bk = __ldg(a.ib + k2);
     if (packed) {
       const float2 v0 = cmul(cmul(make_float2(c1, -c4), bk), ia);
@@ -382,14 +391,27 @@ k_fs2_inv_rows(Dct2dArgs a) {
       v[j] = cmul(cmul(make_float2(c1 - c2, -(c3 + c4)), bk), ia);
     }
   }
-  __syncthreads();
-  first_stage_regs<L, true>(v, s, g);
-  __syncthreads();
-  fft_stages<L, 16, true>(s, g, a.tw2);
+}
 
-  float2* zr0 = Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2);
-  float2* zr1 = Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2);
-  for (int h = g; h < L / 4; h += R::TPS) {  // two columns p = 2h, 2h + 1 per 16-byte store
+// Inverse preprocess: sf holds the two source rows (L floats each, raw);
+// zero_a: the first row is zero (IDXST_IDCT, packed item).  DST-II reads the
+// columns reversed; IDCT_IDXST swaps the reads at k2 and N2-k2 (column 0 zero).
+// The kind is tested once, outside the unrolled loop.
+template <int L, int TPS>
+__device__ __forceinline__ void inv_pre(const float* sf, const Dct2dArgs& a, int k1, bool packed, bool zero_a,
+                                        int g, float2* v) {
+  const float2 ia = __ldg(a.ia + k1);
+  const float2 ih = __ldg(a.ia + a.n1 / 2);
+  if (a.vkind == 1 || a.vkind == 2)
+    inv_pre_loop<L, TPS, true>(sf, a, ia, ih, packed, zero_a, g, v);
+  else
+    inv_pre_loop<L, TPS, false>(sf, a, ia, ih, packed, zero_a, g, v);
+}
+
+// Inverse pairing: row IFFT in s -> workspace rows of k1 and kmir.
+template <int L, int TPS>
+__device__ __forceinline__ void inv_pair(const float2* s, float2* zr0, float2* zr1, bool packed, int g) {
+  for (int h = g; h < L / 4; h += TPS) {  // two columns p = 2h, 2h + 1 per 16-byte store
     const int p = 2 * h;
     const float2 u0 = s[pidx<float2>(p)], u1 = s[pidx<float2>(p + 1)];
     const float2 w0 = s[pidx<float2>(L - 1 - p)], w1 = s[pidx<float2>(L - 2 - p)];
@@ -403,6 +425,137 @@ k_fs2_inv_rows(Dct2dArgs a) {
     }
     *reinterpret_cast<float4*>(zr0 + p) = o0;
     *reinterpret_cast<float4*>(zr1 + p) = o1;
+  }
+}
+
+// Everything of one item after its rows are in shared memory (st: raw rows;
+// s: the item's FFT buffer).  Contains __syncthreads: all threads call it.
+template <int L, bool INV>
+__device__ __forceinline__ void row_item(const Dct2dArgs& a, int b, int k1, const float* st, float2* s, int g,
+                                         bool zero_a) {
+  using R = RowGeom<L>;
+  const bool packed = (k1 == 0);
+  const int kmir = row_mirror(k1, a.n1);
+  float2 v[16];
+  if constexpr (!INV)
+    fwd_split<L, R::TPS>(reinterpret_cast<const float2*>(st), packed, g, v);
+  else
+    inv_pre<L, R::TPS>(st, a, k1, packed, zero_a, g, v);
+  __syncthreads();  // st may alias s: every read of the rows precedes the first stage
+  first_stage_regs<L, INV>(v, s, g);
+  __syncthreads();
+  fft_stages<L, 16, INV>(s, g, a.tw2);
+  if constexpr (!INV) {
+    fwd_post<L, R::TPS>(s, a, a.out + (long long)b * a.out_bstride, k1, kmir, packed, g);
+  } else {
+    float2* Zw = a.work + (long long)b * a.work_bstride;
+    inv_pair<L, R::TPS>(s, Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2),
+                        Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2), packed, g);
+  }
+}
+
+template <int L, bool INV>
+__global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::MINB) k_fs2_rows(Dct2dArgs a) {
+  using R = RowGeom<L>;
+  extern __shared__ float4 srw[];
+  const int li = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
+  float2* s = reinterpret_cast<float2*>(srw) + li * R::LP;
+  const int k1 = blockIdx.x * R::NI + li;
+  const float *ra, *rb;
+  row_sources<L, INV>(a, blockIdx.z, k1, &ra, &rb);
+  stage_two_rows<L, R::TPS>(reinterpret_cast<float*>(s), ra, rb, g);  // raw rows in the FFT buffer
+  __syncthreads();
+  row_item<L, INV>(a, blockIdx.z, k1, reinterpret_cast<const float*>(s), s, g, ra == nullptr);
+}
+
+// Persistent variant: CTA c takes item groups c, c + grid, ...; while it
+// computes one group, the next group's rows (2 NI rows of 4L bytes) arrive by
+// bulk copy in a separate staging buffer.  Every wait is bounded; a wait that
+// gives up sets the device error word, and the CTA waits (bounded) for the
+// copy it issued before it returns.
+template <int L, bool INV>
+__global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::PMINB) k_fs2p_rows(Dct2dArgs a, int batch) {
+  using R = RowGeom<L>;
+  extern __shared__ __align__(128) unsigned char prw[];
+  float* stage = reinterpret_cast<float*>(prw);
+  float2* fbuf = reinterpret_cast<float2*>(prw + R::STAGE);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(prw + R::STAGE + R::SMEM);
+  const int li = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
+  const int upb = a.n1 / 2 / R::NI;  // item groups per batch entry
+  const int nunits = upb * batch;
+  const int nk = (int)blockIdx.x < nunits ? (nunits - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  int issued = 0;  // thread 0: groups whose loads were issued
+
+  auto issue = [&](int k) {  // thread 0
+    const int u = blockIdx.x + k * gridDim.x;
+    const int b = u / upb, k0 = (u % upb) * R::NI;
+    uint32_t bytes = 0;
+    for (int i = 0; i < R::NI; ++i) {
+      const float *ra, *rb;
+      row_sources<L, INV>(a, b, k0 + i, &ra, &rb);
+      bytes += (ra ? 2u : 1u) * 4u * L;
+    }
+    pipe::mbar_arrive_expect_tx(bar, bytes);
+    for (int i = 0; i < R::NI; ++i) {
+      const float *ra, *rb;
+      row_sources<L, INV>(a, b, k0 + i, &ra, &rb);
+      if (ra) pipe::bulk_load(stage + i * 2 * L, ra, 4u * L, bar);
+      pipe::bulk_load(stage + i * 2 * L + L, rb, 4u * L, bar);
+    }
+    ++issued;
+  };
+
+  if (threadIdx.x == 0) {
+    pipe::mbar_init(bar, 1);
+    pipe::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && nk > 0) issue(0);
+  int done = 0;
+  for (int k = 0; k < nk; ++k) {
+    const bool ok = pipe::mbar_wait(bar, k & 1);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      break;
+    }
+    done = k + 1;
+    const int u = blockIdx.x + k * gridDim.x;
+    const int b = u / upb, k1 = (u % upb) * R::NI + li;
+    const float* st = stage + li * 2 * L;
+    float2* s = fbuf + li * R::LP;
+    const float *ra, *rb;
+    row_sources<L, INV>(a, b, k1, &ra, &rb);
+    // row_item reads st, then synchronises before its first stage: the next
+    // group's copy may start after that barrier, so it is issued inside the
+    // item between the two (see below).
+    const bool packed = (k1 == 0);
+    const int kmir = row_mirror(k1, a.n1);
+    float2 v[16];
+    if constexpr (!INV)
+      fwd_split<L, R::TPS>(reinterpret_cast<const float2*>(st), packed, g, v);
+    else
+      inv_pre<L, R::TPS>(st, a, k1, packed, ra == nullptr, g, v);
+    __syncthreads();  // staging consumed by every thread
+    if (threadIdx.x == 0 && k + 1 < nk) {
+      pipe::fence_proxy_async();
+      issue(k + 1);
+    }
+    first_stage_regs<L, INV>(v, s, g);
+    __syncthreads();
+    fft_stages<L, 16, INV>(s, g, a.tw2);
+    if constexpr (!INV) {
+      fwd_post<L, R::TPS>(s, a, a.out + (long long)b * a.out_bstride, k1, kmir, packed, g);
+    } else {
+      float2* Zw = a.work + (long long)b * a.work_bstride;
+      inv_pair<L, R::TPS>(s, Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2),
+                          Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2), packed, g);
+    }
+    __syncthreads();  // FFT buffer consumed before the next first stage
+  }
+  // A copy issued but not waited for (only after a failed wait) must land
+  // before the CTA's shared memory is released.
+  if (threadIdx.x == 0 && issued > done) {
+    if (!pipe::mbar_wait(bar, done & 1)) atomicExch(a.err, 1);
   }
 }
 

@@ -447,6 +447,9 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   a.fsA = fsA;
   a.fsB = fsB;
   a.vkind = p->family == FAM_FS2 ? kind : 0;
+  a.nsm = p->nsm;
+  a.rows_mode = 0;  // GBDCT_FS2_ROWS=persistent|staged selects the fs2 row-pass variant
+  if (const char* rm = getenv("GBDCT_FS2_ROWS")) a.rows_mode = !strcmp(rm, "persistent") ? 1 : 0;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 
