@@ -34,6 +34,8 @@
 #include "fft_r64.cuh"
 #include "pipe.cuh"
 
+#include <type_traits>
+
 namespace gbdct {
 
 constexpr int kCsCols = 128;            // complex columns per column-step CTA
@@ -42,7 +44,7 @@ constexpr int kCsThreads = 4 * kCsCols;  // four threads per column
 template <int N1>
 struct Fs2Geom {
   static constexpr int A = (N1 >= 2048) ? 64 : (N1 >= 512 ? 32 : 16);
-  static constexpr int B = N1 / A;
+  static constexpr int B = N1 / A;  // 128 for N1 = 8192 (vector column steps only)
 };
 
 // Physical workspace row of column-spectrum row k1 (A, B powers of two).
@@ -163,6 +165,293 @@ k_fs2_col(Dct2dArgs a) {
           y = make_float2(sr * y.x, sc * y.y);
         }
         *(reinterpret_cast<float2*>(xo + (long long)row * N2) + col) = y;
+      }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Column steps, vector form (k_fs2_colv): each thread owns CPT adjacent complex
+// columns (CPT = 2: 16-byte loads and stores) and T = S/Q points of each; Q
+// threads share a column group.  DFT_S = DFT_T in registers, twiddle
+// W_S^{q m}, one exchange through shared memory, then DFT_Q across the Q
+// threads (S = Q T: W_S^{(q + Q j)(m + T p)} = W_S^{q m} W_Q^{q p} W_T^{j m}).
+//   S = 16: Q 4, CPT 2;  S = 32: Q 4, CPT 2;  S = 64: Q 8, CPT 2;
+//   S = 128: Q 8, CPT 1 (N1 = 8192).
+// ----------------------------------------------------------------------------
+
+// cos(2 pi k / 128), k = 0..127 (float roundings of the exact values)
+__host__ __device__ constexpr float cos128(int k) {
+  constexpr float t[128] = {
+    1.000000000e+00f,
+    9.987954562e-01f,
+    9.951847267e-01f,
+    9.891765100e-01f,
+    9.807852804e-01f,
+    9.700312532e-01f,
+    9.569403357e-01f,
+    9.415440652e-01f,
+    9.238795325e-01f,
+    9.039892931e-01f,
+    8.819212643e-01f,
+    8.577286100e-01f,
+    8.314696123e-01f,
+    8.032075315e-01f,
+    7.730104534e-01f,
+    7.409511254e-01f,
+    7.071067812e-01f,
+    6.715589548e-01f,
+    6.343932842e-01f,
+    5.956993045e-01f,
+    5.555702330e-01f,
+    5.141027442e-01f,
+    4.713967368e-01f,
+    4.275550934e-01f,
+    3.826834324e-01f,
+    3.368898534e-01f,
+    2.902846773e-01f,
+    2.429801799e-01f,
+    1.950903220e-01f,
+    1.467304745e-01f,
+    9.801714033e-02f,
+    4.906767433e-02f,
+    6.123233996e-17f,
+    -4.906767433e-02f,
+    -9.801714033e-02f,
+    -1.467304745e-01f,
+    -1.950903220e-01f,
+    -2.429801799e-01f,
+    -2.902846773e-01f,
+    -3.368898534e-01f,
+    -3.826834324e-01f,
+    -4.275550934e-01f,
+    -4.713967368e-01f,
+    -5.141027442e-01f,
+    -5.555702330e-01f,
+    -5.956993045e-01f,
+    -6.343932842e-01f,
+    -6.715589548e-01f,
+    -7.071067812e-01f,
+    -7.409511254e-01f,
+    -7.730104534e-01f,
+    -8.032075315e-01f,
+    -8.314696123e-01f,
+    -8.577286100e-01f,
+    -8.819212643e-01f,
+    -9.039892931e-01f,
+    -9.238795325e-01f,
+    -9.415440652e-01f,
+    -9.569403357e-01f,
+    -9.700312532e-01f,
+    -9.807852804e-01f,
+    -9.891765100e-01f,
+    -9.951847267e-01f,
+    -9.987954562e-01f,
+    -1.000000000e+00f,
+    -9.987954562e-01f,
+    -9.951847267e-01f,
+    -9.891765100e-01f,
+    -9.807852804e-01f,
+    -9.700312532e-01f,
+    -9.569403357e-01f,
+    -9.415440652e-01f,
+    -9.238795325e-01f,
+    -9.039892931e-01f,
+    -8.819212643e-01f,
+    -8.577286100e-01f,
+    -8.314696123e-01f,
+    -8.032075315e-01f,
+    -7.730104534e-01f,
+    -7.409511254e-01f,
+    -7.071067812e-01f,
+    -6.715589548e-01f,
+    -6.343932842e-01f,
+    -5.956993045e-01f,
+    -5.555702330e-01f,
+    -5.141027442e-01f,
+    -4.713967368e-01f,
+    -4.275550934e-01f,
+    -3.826834324e-01f,
+    -3.368898534e-01f,
+    -2.902846773e-01f,
+    -2.429801799e-01f,
+    -1.950903220e-01f,
+    -1.467304745e-01f,
+    -9.801714033e-02f,
+    -4.906767433e-02f,
+    -1.836970199e-16f,
+    4.906767433e-02f,
+    9.801714033e-02f,
+    1.467304745e-01f,
+    1.950903220e-01f,
+    2.429801799e-01f,
+    2.902846773e-01f,
+    3.368898534e-01f,
+    3.826834324e-01f,
+    4.275550934e-01f,
+    4.713967368e-01f,
+    5.141027442e-01f,
+    5.555702330e-01f,
+    5.956993045e-01f,
+    6.343932842e-01f,
+    6.715589548e-01f,
+    7.071067812e-01f,
+    7.409511254e-01f,
+    7.730104534e-01f,
+    8.032075315e-01f,
+    8.314696123e-01f,
+    8.577286100e-01f,
+    8.819212643e-01f,
+    9.039892931e-01f,
+    9.238795325e-01f,
+    9.415440652e-01f,
+    9.569403357e-01f,
+    9.700312532e-01f,
+    9.807852804e-01f,
+    9.891765100e-01f,
+    9.951847267e-01f,
+    9.987954562e-01f
+
+  };
+  return t[k & 127];
+}
+
+// a * W_R^E for R dividing 128, W_R = exp(-2 pi i / R) (forward) or exp(+2 pi i / R).
+template <int R, int E, bool INV, typename T>
+__device__ __forceinline__ T mul_w128(T a) {
+  constexpr int e = ((E * (128 / R)) % 128 + 128) % 128;
+  constexpr float c = cos128(e);
+  constexpr float s = cos128((160 - e) % 128);  // sin(2 pi e / 128) = cos(2 pi (32 - e) / 128)
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr (e == 32) {
+    return mul_mj<INV>(a);
+  } else if constexpr (e == 64) {
+    return cneg(a);
+  } else if constexpr (e == 96) {
+    return mul_mj<!INV>(a);
+  } else if constexpr (e % 32 == 16) {
+    return cmul_diag(a, c, (INV ? s : -s) / c);
+  } else {
+    return cmulk(a, c, INV ? s : -s);
+  }
+}
+
+template <int S>
+struct ColCfg {
+  static constexpr int Q = S >= 64 ? 8 : 4;           // threads per column group
+  static constexpr int CPT = S >= 128 ? 1 : 2;        // complex columns per thread
+  static constexpr int T = S / Q;                     // points per column per thread
+  static constexpr int COLS = S >= 128 ? 64 : 128;    // complex columns per CTA
+  static constexpr int NG = COLS / CPT;               // column groups per CTA
+  static constexpr int THREADS = NG * Q;
+  static constexpr size_t SMEM = (size_t)S * COLS * sizeof(float2);
+  using V = typename std::conditional<CPT == 2, float4, float2>::type;
+};
+
+// x[m] *= W_S^{q m} (m < T) for the thread's warp-uniform q < Q.
+template <int S, int Q, int T, bool INV, typename V>
+__device__ __forceinline__ void colv_twiddle(V* x, int q) {
+  r64::static_for<1, Q>([&](auto qc) {
+    constexpr int qq = decltype(qc)::value;
+    if (q == qq) {
+      r64::static_for<1, T>([&](auto mc) {
+        constexpr int m = decltype(mc)::value;
+        x[m] = mul_w128<S, qq * m, INV>(x[m]);
+      });
+    }
+  });
+}
+
+// DFT_S along the slab rows: on entry x[j] = slab row q + Q j (j < T); on return
+// x[i Q + p] = output row (q T/Q + i) + T p  (i < T/Q, p < Q).
+template <int S, bool INV, typename V>
+__device__ __forceinline__ void colv_dft(V* x, int q, int c, V* ex) {
+  using C = ColCfg<S>;
+  constexpr int Q = C::Q, T = C::T, NG = C::NG, TQ = T / Q;
+  dft<T, INV>(x);
+  colv_twiddle<S, Q, T, INV>(x, q);
+#pragma unroll
+  for (int m = 0; m < T; ++m) ex[(q * T + m) * NG + c] = x[m];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < TQ; ++i) {
+    const int m = q * TQ + i;
+    V y[Q];
+#pragma unroll
+    for (int p = 0; p < Q; ++p) y[p] = ex[(p * T + m) * NG + c];
+    dft<Q, INV>(y);
+#pragma unroll
+    for (int p = 0; p < Q; ++p) x[i * Q + p] = y[p];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float2 vsign(float2 v, float sr, float sc) { return make_float2(sr * v.x, sc * v.y); }
+__device__ __forceinline__ float4 vsign(float4 v, float sr, float sc) {
+  return make_float4(sr * v.x, sc * v.y, sr * v.z, sc * v.w);
+}
+
+template <int N1, int KIND>
+__global__ void __launch_bounds__(ColCfg<(KIND == 0 || KIND == 3) ? Fs2Geom<N1>::B : Fs2Geom<N1>::A>::THREADS,
+                                  1024 / ColCfg<(KIND == 0 || KIND == 3) ? Fs2Geom<N1>::B : Fs2Geom<N1>::A>::THREADS)
+k_fs2_colv(Dct2dArgs a) {
+  using G = Fs2Geom<N1>;
+  constexpr bool INV = KIND >= 2;
+  constexpr int S = (KIND == 0 || KIND == 3) ? G::B : G::A;
+  using C = ColCfg<S>;
+  using V = typename C::V;
+  constexpr int T = C::T, Q = C::Q, TQ = T / Q;
+  extern __shared__ float4 scv[];
+  V* ex = reinterpret_cast<V*>(scv);
+  const int c = threadIdx.x % C::NG, q = threadIdx.x / C::NG;
+  const int r = blockIdx.x;
+  const int N2 = a.n2;
+  const long long hv = N2 / 2 / C::CPT;  // V elements per workspace row
+  const int colv = blockIdx.y * C::NG + c;  // V index within a row
+  V* W = reinterpret_cast<V*>(a.work + (long long)blockIdx.z * a.work_bstride);
+
+  V x[T];
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    const int i = q + Q * j;  // slab row of this input
+    if constexpr (KIND == 0) {
+      const float* xin = a.in + (long long)blockIdx.z * a.in_bstride;
+      const int row = reorder_src(r + G::A * i, N1);
+      x[j] = reinterpret_cast<const V*>(xin + (long long)row * N2)[colv];
+      if (a.vkind == 1) {  // DST-II: (-1)^(n1 + n2); real columns alternate in parity
+        const float sr = (row & 1) ? -1.f : 1.f;
+        x[j] = vsign(x[j], sr, -sr);
+      }
+    } else if constexpr (KIND == 3) {
+      x[j] = W[(long long)(i * G::A + r) * hv + colv];
+    } else {
+      x[j] = W[(long long)(r * G::A + i) * hv + colv];
+    }
+  }
+  colv_dft<S, INV>(x, q, c, ex);
+#pragma unroll
+  for (int i = 0; i < TQ; ++i)
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+      const int o = q * TQ + i + T * p;  // k1b (KIND 0), k1a (1), n1a (2), n1b (3)
+      V y = x[i * Q + p];
+      if constexpr (KIND == 0) {
+        y = cmul(y, __ldg(a.fstw + r * G::B + o));
+        W[(long long)(o * G::A + r) * hv + colv] = y;
+      } else if constexpr (KIND == 2) {
+        y = cmulc(y, __ldg(a.fstw + o * G::B + r));
+        W[(long long)(r * G::A + o) * hv + colv] = y;
+      } else if constexpr (KIND == 1) {
+        W[(long long)(r * G::A + o) * hv + colv] = y;
+      } else {
+        float* xo = a.out + (long long)blockIdx.z * a.out_bstride;
+        const int row = reorder_src(r + G::A * o, N1);
+        if (a.vkind) {  // output signs: (-1)^(n1+n2) DST-II, (-1)^n2 IDCT_IDXST, (-1)^n1 IDXST_IDCT
+          const float sr = (a.vkind != 2 && (row & 1)) ? -1.f : 1.f;
+          const float sc = (a.vkind != 3) ? -sr : sr;
+          y = vsign(y, sr, sc);
+        }
+        reinterpret_cast<V*>(xo + (long long)row * N2)[colv] = y;
       }
     }
 }

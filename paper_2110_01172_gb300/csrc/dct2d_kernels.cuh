@@ -60,6 +60,7 @@ struct Dct2dArgs {
   int vkind;          // kind whose index/sign maps the fs2 kernels fold into their
                       // loads and stores (0: DCT-II, no map; see dct2d_fs2_kernels.cuh)
   int rows_mode;      // host side only (fs2): 0 staged row passes, 1 persistent prefetching row passes
+  int cols_mode;      // host side only (fs2): 0 vector column steps, 1 scalar (one column per thread)
   int nsm;            // host side only: multiprocessors of the device
 };
 

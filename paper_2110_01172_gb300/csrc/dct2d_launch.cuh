@@ -75,10 +75,10 @@ constexpr int kFsMinLog2N1 = 10, kFsMaxLog2N1 = 12, kFsMinLog2N2 = 12, kFsMaxLog
 cudaError_t run_fsp(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int batch, int nsm, cudaStream_t s,
                     bool prepare);
 
-// Occupancy-first four-step family: N1 in {256, ..., 4096}, N2 in {256, ..., 16384}.
+// Occupancy-first four-step family: N1 in {256, ..., 8192}, N2 in {256, ..., 16384}.
 cudaError_t run_fs2(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s,
                     bool prepare);
-constexpr int kFs2MinLog2N1 = 8, kFs2MaxLog2N1 = 12, kFs2MinLog2N2 = 8, kFs2MaxLog2N2 = 14;
+constexpr int kFs2MinLog2N1 = 8, kFs2MaxLog2N1 = 13, kFs2MinLog2N2 = 8, kFs2MaxLog2N2 = 14;
 inline void fs2_split(int log2N1, int* A, int* B) {
   const int n1 = 1 << log2N1;
   *A = (n1 >= 2048) ? 64 : (n1 >= 512 ? 32 : 16);

@@ -44,8 +44,8 @@ struct gbdct_plan_s {
 namespace {
 
 // Kernel families (all compute the same transform; chosen by size):
-//   FAM_FS2  four-step column steps (4 threads per column) + 16-point-per-thread
-//            row passes, N1 in {256..4096}, N2 in {256..16384}
+//   FAM_FS2  four-step column steps + 16-point-per-thread row passes,
+//            N1 in {256..8192}, N2 in {256..16384}
 //   FAM_FSP  FAM_FS as persistent TMA-bulk-copy pipelines, N1 in {1024..4096}, N2 = 4096
 //   FAM_FS   four-step column FFTs + radix-64 rows, N1 in {1024..4096}, N2 in {4096, 8192}
 //   FAM_R64  radix-64 register FFTs, N1 and N2 in {4096, 8192}
@@ -450,6 +450,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   a.nsm = p->nsm;
   a.rows_mode = 0;  // GBDCT_FS2_ROWS=persistent|staged selects the fs2 row-pass variant
   if (const char* rm = getenv("GBDCT_FS2_ROWS")) a.rows_mode = !strcmp(rm, "persistent") ? 1 : 0;
+  a.cols_mode = 0;  // GBDCT_FS2_COLS=scalar|vector selects the fs2 column-step form (N1 <= 4096)
+  if (const char* cm = getenv("GBDCT_FS2_COLS")) a.cols_mode = !strcmp(cm, "scalar") ? 1 : 0;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 

@@ -8,13 +8,27 @@ template <int N1, int KIND>
 cudaError_t col_launch(const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
   using G = Fs2Geom<N1>;
   constexpr int S = (KIND == 0 || KIND == 3) ? G::B : G::A;
-  constexpr size_t smem = (size_t)S * kCsCols * sizeof(float2);
-  if (prepare) {
-    return cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_col<N1, KIND>),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
+  using C = ColCfg<S>;
+  constexpr bool kScalar = S <= 64;  // the scalar (one column per thread) form covers S <= 64
+  constexpr size_t smem_s = (size_t)S * kCsCols * sizeof(float2);
   const int nslab = (KIND == 0 || KIND == 3) ? G::A : G::B;
-  k_fs2_col<N1, KIND><<<dim3(nslab, a.n2 / 2 / kCsCols, batch), kCsThreads, smem, s>>>(a);
+  if (prepare) {
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_colv<N1, KIND>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if constexpr (kScalar) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_col<N1, KIND>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    }
+    return e;
+  }
+  if constexpr (kScalar) {
+    if (a.cols_mode == 1) {
+      k_fs2_col<N1, KIND><<<dim3(nslab, a.n2 / 2 / kCsCols, batch), kCsThreads, smem_s, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  k_fs2_colv<N1, KIND><<<dim3(nslab, a.n2 / 2 / C::COLS, batch), C::THREADS, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -38,6 +52,7 @@ cudaError_t run_fs2_col(int lg1, int kind, const Dct2dArgs& a, int batch, cudaSt
     case 10: return cols_impl<1024>(kind, a, batch, s, prepare);
     case 11: return cols_impl<2048>(kind, a, batch, s, prepare);
     case 12: return cols_impl<4096>(kind, a, batch, s, prepare);
+    case 13: return cols_impl<8192>(kind, a, batch, s, prepare);
   }
   return cudaErrorInvalidValue;
 }

@@ -149,12 +149,13 @@ FAMILY_SUPPORT = {
     "r64": lambda s: all(n in (4096, 8192) for n in s),
     "fs": lambda s: s[0] in (1024, 2048, 4096) and s[1] in (4096, 8192),
     "fsp": lambda s: s[0] in (1024, 2048, 4096) and s[1] == 4096,
-    "fs2": lambda s: 256 <= s[0] <= 4096 and 256 <= s[1] <= 16384,
+    "fs2": lambda s: 256 <= s[0] <= 8192 and 256 <= s[1] <= 16384,
 }
 
 
 @pytest.mark.parametrize("family", ["seq", "pair", "r64", "fs", "fsp", "fs2"])
-@pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192), (1024, 4096)])
+@pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192), (1024, 4096),
+                                   (8192, 2048)])
 def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
     """Each kernel family, forced through GBDCT_KERNEL_FAMILY, on the same inputs."""
     if not FAMILY_SUPPORT[family](shape):
@@ -205,7 +206,8 @@ def test_batched_four_step_families(family, monkeypatch):
 
 
 @pytest.mark.parametrize("family", ["seq", "pair", "fs2"])
-@pytest.mark.parametrize("shape", [(256, 512), (64, 2048), (256, 256), (512, 256), (2048, 256), (256, 16384)])
+@pytest.mark.parametrize("shape", [(256, 512), (64, 2048), (256, 256), (512, 256), (2048, 256), (256, 16384),
+                                   (8192, 256)])
 def test_small_families_full_oracle(family, shape, monkeypatch):
     if not FAMILY_SUPPORT[family](shape):
         pytest.skip(f"{family} does not support {shape}")
