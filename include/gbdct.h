@@ -105,11 +105,17 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
                                        int64_t batch, int kind, int dtype);
 
 /*
- * Forward transform.  `in` and `out` are device pointers to batch * prod(dims)
- * float32 values, 16-byte aligned; in == out (in place) is allowed.  The call
- * is asynchronous on `stream`; the caller keeps both buffers alive until the
- * stream has passed the work.  Errors: INVALID_ARG (NULL or misaligned
- * pointer, NULL plan), CUDA (launch failure).
+ * Forward transform.  `in` and `out` point to batch * prod(dims) float32
+ * values, 16-byte aligned; in == out (in place) is allowed.  Each may be
+ * memory of the plan's device, managed memory, or page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister, mapped at the same address): host
+ * buffers are read and written by the transform's own first and last kernels
+ * over the host link, with no staging copy.  Pageable host memory is accepted
+ * only where the device can access it (cudaDevAttrPageableMemoryAccess).  The
+ * call is asynchronous on `stream`; the caller keeps both buffers alive until
+ * the stream has passed the work.  Errors: INVALID_ARG (NULL, misaligned or
+ * inaccessible pointer — e.g. another device's memory — NULL plan), CUDA
+ * (launch failure).
  */
 gbdct_status gbdct_exec_forward(gbdct_plan_t plan, const void* in, void* out, void* stream);
 

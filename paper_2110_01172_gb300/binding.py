@@ -179,32 +179,38 @@ class Plan:
         return int(self._lib.gbdct_plan_launches_per_exec(self._h))
 
     def _prep(self, x, out):
+        """x and out: CUDA float32 tensors, or page-locked CPU float32 tensors
+        (read/written by the kernels over the host link, no staging copy)."""
         torch = _torch()
         want = ((self.batch,) if self.batch > 1 else ()) + self.shape
-        if x.dtype != torch.float32 or not x.is_cuda:
-            raise TypeError("expected a CUDA float32 tensor")
+
+        def usable(t):
+            return t.dtype == torch.float32 and (t.is_cuda or (t.device.type == "cpu" and t.is_pinned()))
+
+        if not usable(x):
+            raise TypeError("expected a CUDA or page-locked CPU float32 tensor")
         if tuple(x.shape) != want:
             raise ValueError(f"expected shape {want}, got {tuple(x.shape)}")
         if not x.is_contiguous():
             x = x.contiguous()
         if out is None:
-            out = torch.empty_like(x)
-        elif tuple(out.shape) != want or out.dtype != torch.float32 or not out.is_contiguous():
-            raise ValueError("out must be a contiguous float32 tensor of the input's shape")
+            out = torch.empty_like(x) if x.is_cuda else torch.empty(want, dtype=torch.float32, pin_memory=True)
+        elif tuple(out.shape) != want or not usable(out) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CUDA or page-locked float32 tensor of the input's shape")
         return x, out
 
     def forward(self, x, out=None, stream=None):
         x, out = self._prep(x, out)
         _check(self._lib.gbdct_exec_forward(self._h, ctypes.c_void_p(x.data_ptr()),
                                             ctypes.c_void_p(out.data_ptr()),
-                                            _stream_handle(stream, x.device)), "gbdct_exec_forward")
+                                            _stream_handle(stream, self.device)), "gbdct_exec_forward")
         return out
 
     def inverse(self, x, out=None, stream=None):
         x, out = self._prep(x, out)
         _check(self._lib.gbdct_exec_inverse(self._h, ctypes.c_void_p(x.data_ptr()),
                                             ctypes.c_void_p(out.data_ptr()),
-                                            _stream_handle(stream, x.device)), "gbdct_exec_inverse")
+                                            _stream_handle(stream, self.device)), "gbdct_exec_inverse")
         return out
 
     def step(self, inverse: bool, step: int, x, out, stream=None):

@@ -173,6 +173,32 @@ struct DeviceGuard {
   }
 };
 
+// True when kernels on `device` may dereference `ptr`: this device's memory,
+// managed memory, page-locked host memory mapped at the same address (read
+// and written over the host link by the kernels themselves), or any host
+// memory when the device can access pageable memory.  While `s` is capturing
+// a graph the check is skipped (the pointers of a captured launch are the
+// caller's own device buffers, and the query is not needed there).
+bool device_accessible(const void* ptr, int device, cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) return true;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice: return at.device == device;
+    case cudaMemoryTypeManaged: return true;
+    case cudaMemoryTypeHost: return at.devicePointer == ptr;
+    default: {
+      int pageable = 0;
+      cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+      return pageable != 0;
+    }
+  }
+}
+
 void free_plan(gbdct_plan_s* p) {
   if (!p) return;
   if (p->inner) gbdct_plan_destroy(p->inner);
@@ -518,6 +544,7 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
   if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return GBDCT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!device_accessible(in, p->device, s) || !device_accessible(out, p->device, s)) return GBDCT_ERR_INVALID_ARG;
   if (p->ndim == 3) return exec3d(p, in, out, s, inverse, step);
   if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse, step);
   if (!inverse && (p->kind == GBDCT_IDCT_IDXST || p->kind == GBDCT_IDXST_IDCT)) return GBDCT_ERR_UNSUPPORTED;
