@@ -265,8 +265,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": us / 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"2D DCT-II + inverse {n1}x{n2}, U[-1,1] seed 0",
-                   "shape": [n1, n2], "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOAD if (n1, n2) == (N1, N2) else
+                   f"2D DCT-II + inverse (DCT-III) {n1}x{n2} FP32, U[-1,1] seed 0",
+                   "shape": [n1, n2], "parallelism": "replicas1", "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": us, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"full {n1}x{n2} step (FP64 separable direct sums), "
                                    f"BLAS threads = default ({cores} cores)"},
