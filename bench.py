@@ -48,15 +48,15 @@ FALLBACK_HBM_GBS = 6800.0
 # from the ncu capture summarised in profiles/, valid only for the kernel
 # sources with this digest (otherwise reported as null).
 TRAFFIC = {
-    "sources_sha256": "39110cbe20d6865507c9cddf4fa0666816212b952b5a08d76274d44b5a768e73",
+    "sources_sha256": "486108fabd254ea208ae9fe23ae8ee4da1af0811d04fbaf102aff625a15d2e16",
     "family": "fs2",
     "bytes_per_launch": {   # profiles/fs2_kernels_4096_ncu.md (cold L2 under ncu)
-        "forward column step C1 (reorder + DFT_B + twiddle)": 67165440 + 17367040,
-        "forward column step C2 (DFT_A)": 67122432 + 6613760,
-        "forward row pass (split + row FFT + postprocess)": 67231488 + 17267456,
-        "inverse row pass (preprocess + row IFFT + pairing)": 67238144 + 16097792,
-        "inverse column step C2' (DFT_A + twiddle)": 67156992 + 6772224,
-        "inverse column step C1' (DFT_B + inverse reorder)": 67128576 + 17273856,
+        "forward column step C1 (reorder + DFT_B + twiddle)": 67166720 + 18386432,
+        "forward column step C2 (DFT_A)": 67124480 + 6780672,
+        "forward row pass (split + row FFT + postprocess)": 67223552 + 17459712,
+        "inverse row pass (preprocess + row IFFT + pairing)": 67238144 + 16174848,
+        "inverse column step C2' (DFT_A + twiddle)": 67159552 + 6728192,
+        "inverse column step C1' (DFT_B + inverse reorder)": 67130880 + 17167360,
     },
 }
 
