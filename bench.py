@@ -309,6 +309,66 @@ def run_serving(args, dev):
     return out
 
 
+def load_baselines():
+    """ctypes handle to the comparison baselines (B1: cuFFT three-stage, B2:
+    row-column); builds them if needed.  Raises if they cannot be built."""
+    import ctypes
+    sys.path.insert(0, ROOT)
+    from paper_2110_01172_gb300 import build as _b
+    lib = ctypes.CDLL(_b.build_baselines())
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    for name, args in (("gbdct_b1_create", [ctypes.POINTER(vp), i, i]), ("gbdct_b1_forward", [vp, vp, vp, vp]),
+                       ("gbdct_b1_inverse", [vp, vp, vp, vp]), ("gbdct_b1_destroy", [vp]),
+                       ("gbdct_b2_create", [ctypes.POINTER(vp), i, i]), ("gbdct_b2_forward", [vp, vp, vp, vp]),
+                       ("gbdct_b2_destroy", [vp])):
+        fn = getattr(lib, name)
+        fn.restype = i
+        fn.argtypes = args
+    return lib
+
+
+def run_baselines(dev, n1, n2, ours_fwd_us, ours_inv_us, peak):
+    """B1 and B2 timed like the product (CUDA events, two rotating buffer sets
+    larger than L2 together) on the same GPU; checked against our forward."""
+    import ctypes
+    import torch
+    try:
+        lib = load_baselines()
+    except Exception as e:
+        return {"unavailable": str(e).splitlines()[0]}
+    from paper_2110_01172_gb300 import Plan
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    xs = [torch.rand(n1, n2, device=dev) * 2 - 1 for _ in range(2)]
+    ys = [torch.empty_like(xs[0]) for _ in range(2)]
+    out = {}
+    h1, h2 = ctypes.c_void_p(), ctypes.c_void_p()
+    if lib.gbdct_b1_create(ctypes.byref(h1), n1, n2) != 0 or lib.gbdct_b2_create(ctypes.byref(h2), n1, n2) != 0:
+        return {"unavailable": "baseline plan creation failed"}
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    b1f = _event_loop_us(lambda i: lib.gbdct_b1_forward(h1, ptr(xs[i % 2]), ptr(ys[i % 2]), sp), 20, stream)
+    b1i = _event_loop_us(lambda i: lib.gbdct_b1_inverse(h1, ptr(ys[i % 2]), ptr(xs[i % 2]), sp), 20, stream)
+    b2f = _event_loop_us(lambda i: lib.gbdct_b2_forward(h2, ptr(xs[i % 2]), ptr(ys[i % 2]), sp), 20, stream)
+    # agreement with the product's forward on the same input
+    plan = Plan((n1, n2))
+    ref = plan.forward(xs[0])
+    lib.gbdct_b1_forward(h1, ptr(xs[0]), ptr(ys[0]), sp)
+    d1 = ((ys[0] - ref).norm() / ref.norm()).item()
+    lib.gbdct_b2_forward(h2, ptr(xs[0]), ptr(ys[1]), sp)
+    d2 = ((ys[1] - ref).norm() / ref.norm()).item()
+    torch.cuda.synchronize()
+    lib.gbdct_b1_destroy(h1)
+    lib.gbdct_b2_destroy(h2)
+    algo = 8.0 * n1 * n2
+    out["b1_cufft_three_stage"] = {"fwd_us": b1f, "inv_us": b1i, "fwd_frac": algo / (b1f * 1e-6) / 1e9 / peak,
+                                   "rel_l2_vs_ours": d1, "ours_speedup_fwd": b1f / ours_fwd_us,
+                                   "ours_speedup_inv": b1i / ours_inv_us}
+    out["b2_row_column"] = {"fwd_us": b2f, "fwd_frac": algo / (b2f * 1e-6) / 1e9 / peak,
+                            "rel_l2_vs_ours": d2, "ours_speedup_fwd": b2f / ours_fwd_us}
+    out["note"] = "comparison builds around cuFFT (own pre/post kernels), not the product"
+    return out
+
+
 def _event_loop_us(fn, iters, stream):
     import torch
     e0 = torch.cuda.Event(enable_timing=True)
@@ -496,6 +556,7 @@ def run_ours(args):
     if not args.no_serve:
         serve = run_serving(args, dev)
     configs = None if args.no_configs else run_configs(dev, measured_peaks()[0])
+    baselines = None if args.no_configs else run_baselines(dev, n1, n2, fwd_us, inv_us, measured_peaks()[0])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -525,6 +586,7 @@ def run_ours(args):
             "kernel_family": plan.family,
             "serve": serve,
             "configs": configs,
+            "baselines": baselines,
             "e2e": {"value": e2e_us, "unit": UNIT, "h2d_bytes_per_step": 4 * n1 * n2,
                     "d2h_bytes_per_step": 4 * n1 * n2,
                     "mode": "host buffers read/written by the first/last kernels",

@@ -85,6 +85,31 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     return library_path()
 
 
+BASELINE_LIB = "libgbdct_baselines.so"
+BASELINE_SRC = os.path.join(CSRC, "baselines", "cufft_baselines.cu")
+
+
+def baselines_path() -> str:
+    return os.path.join(BUILD, BASELINE_LIB)
+
+
+def build_baselines(force: bool = False) -> str:
+    """Comparison baselines (cuFFT three-stage and row-column) in their own
+    library, linked against cuFFT; the transform library does not use them."""
+    out = baselines_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) > max(
+            os.path.getmtime(BASELINE_SRC), os.path.getmtime(os.path.abspath(__file__))):
+        return out
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = out + ".tmp"
+    cmd = [nvcc_path(), *ARCH, *NVCC_FLAGS, "-shared", BASELINE_SRC, "-o", tmp, "-lcufft", "-lcudart_static"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"baseline build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, out)
+    return out
+
+
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
