@@ -152,6 +152,10 @@ class PoissonServer:
                 return None
             self.pool[victim].pop().close()
             self.admission.release(request_bytes(victim))
+        return self._make(shape)
+
+    def _make(self, shape):
+        """New resident resources for `shape` (the only place that creates them)."""
         return _Resources(shape, self.device, graph=self.graphs)
 
     def _release(self, res):
