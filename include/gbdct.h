@@ -211,6 +211,11 @@ typedef struct gbdct_multi_s* gbdct_multi_t;
 #define GBDCT_MULTI_GRAPH 1
 #define GBDCT_MULTI_TUNE 2
 gbdct_status gbdct_multi_create(gbdct_multi_t* out, int count, const int64_t* shapes, int kind, int flags);
+/* The packed layout gbdct_multi_create would use, computed on the host with
+ * no CUDA call: offsets[i] (optional, count entries) receives the offset in
+ * floats of transform i, *groups (optional) the number of shape groups.
+ * Returns the floats in a packed buffer, or -1 for invalid shapes. */
+int64_t gbdct_multi_layout(int count, const int64_t* shapes, int64_t* offsets, int* groups);
 /* Offset (floats) of transform `index` in the packed buffers; -1 if out of range or NULL. */
 int64_t gbdct_multi_offset(gbdct_multi_t m, int index);
 /* Floats in a packed buffer (0 for NULL). */

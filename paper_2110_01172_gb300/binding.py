@@ -93,6 +93,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
                                                        ctypes.c_char_p, ctypes.c_size_t]),
             "gbdct_multi_create": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int, c_i64p, ctypes.c_int,
                                                   ctypes.c_int]),
+            "gbdct_multi_layout": (ctypes.c_int64, [ctypes.c_int, c_i64p, c_i64p, ctypes.POINTER(ctypes.c_int)]),
             "gbdct_multi_offset": (ctypes.c_int64, [plan_p, ctypes.c_int]),
             "gbdct_multi_total_elems": (ctypes.c_int64, [plan_p]),
             "gbdct_multi_group_count": (ctypes.c_int, [plan_p]),
@@ -246,6 +247,20 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def multi_layout(shapes):
+    """(offsets, total floats, groups) of the packed layout of an uneven batch;
+    host-only (no CUDA call)."""
+    lib = load()
+    n = len(shapes)
+    flat = (ctypes.c_int64 * (2 * n))(*[int(v) for sh in shapes for v in sh])
+    offs = (ctypes.c_int64 * n)()
+    groups = ctypes.c_int()
+    total = int(lib.gbdct_multi_layout(n, flat, offs, ctypes.byref(groups)))
+    if total < 0:
+        raise ValueError("invalid shapes for an uneven batch")
+    return list(offs), total, groups.value
 
 
 class MultiPlan:

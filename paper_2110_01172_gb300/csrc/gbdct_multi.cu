@@ -262,16 +262,73 @@ gbdct_status enqueue(gbdct_multi_s* m, bool inverse, const float* in, float* out
 
 }  // namespace
 
+namespace {
+
+// Shape groups in execution order (largest transforms first), each at most
+// 65535 transforms: (n1, n2, member indices).
+struct LayoutGroup {
+  int64_t n1, n2;
+  std::vector<int> members;
+};
+
+std::vector<LayoutGroup> plan_layout(int count, const int64_t* shapes, std::vector<int64_t>* offsets,
+                                     int64_t* total) {
+  std::map<std::pair<int64_t, int64_t>, std::vector<int>> by_shape;
+  for (int i = 0; i < count; ++i) by_shape[{shapes[2 * i], shapes[2 * i + 1]}].push_back(i);
+  std::vector<std::pair<std::pair<int64_t, int64_t>, std::vector<int>>> order(by_shape.begin(), by_shape.end());
+  std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
+    return x.first.first * x.first.second > y.first.first * y.first.second;
+  });
+  std::vector<LayoutGroup> groups;
+  offsets->assign(count, 0);
+  int64_t off = 0;
+  for (auto& kv : order) {
+    const int64_t sz = kv.first.first * kv.first.second;
+    for (size_t b0 = 0; b0 < kv.second.size(); b0 += 65535) {
+      const size_t cnt = std::min<size_t>(65535, kv.second.size() - b0);
+      LayoutGroup g{kv.first.first, kv.first.second, {}};
+      for (size_t j = 0; j < cnt; ++j) {
+        const int idx = kv.second[b0 + j];
+        g.members.push_back(idx);
+        (*offsets)[idx] = off + (int64_t)j * sz;
+      }
+      off += (int64_t)cnt * sz;
+      groups.push_back(std::move(g));
+    }
+  }
+  *total = off;
+  return groups;
+}
+
+gbdct_status check_shapes(int count, const int64_t* shapes) {
+  if (!shapes || count < 1) return GBDCT_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (shapes[2 * i] <= 0 || shapes[2 * i + 1] <= 0) return GBDCT_ERR_INVALID_ARG;
+    if (!pow2_in(shapes[2 * i], 1, 14) || !pow2_in(shapes[2 * i + 1], 1, 14)) return GBDCT_ERR_UNSUPPORTED;
+  }
+  return GBDCT_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int64_t gbdct_multi_layout(int count, const int64_t* shapes, int64_t* offsets, int* groups) {
+  if (check_shapes(count, shapes) != GBDCT_OK) return -1;
+  std::vector<int64_t> offs;
+  int64_t total = 0;
+  const std::vector<LayoutGroup> g = plan_layout(count, shapes, &offs, &total);
+  if (offsets)
+    for (int i = 0; i < count; ++i) offsets[i] = offs[i];
+  if (groups) *groups = (int)g.size();
+  return total;
+}
 
 gbdct_status gbdct_multi_create(gbdct_multi_t* out, int count, const int64_t* shapes, int kind, int flags) {
   if (!out || !shapes || count < 1) return GBDCT_ERR_INVALID_ARG;
   if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
   if (flags & ~(GBDCT_MULTI_GRAPH | GBDCT_MULTI_TUNE)) return GBDCT_ERR_INVALID_ARG;
-  for (int i = 0; i < count; ++i) {
-    if (shapes[2 * i] <= 0 || shapes[2 * i + 1] <= 0) return GBDCT_ERR_INVALID_ARG;
-    if (!pow2_in(shapes[2 * i], 1, 14) || !pow2_in(shapes[2 * i + 1], 1, 14)) return GBDCT_ERR_UNSUPPORTED;
-  }
+  if (const gbdct_status cs = check_shapes(count, shapes)) return cs;
   gbdct_multi_s* m = new (std::nothrow) gbdct_multi_s();
   if (!m) return GBDCT_ERR_OOM;
   m->kind = kind;
@@ -282,29 +339,17 @@ gbdct_status gbdct_multi_create(gbdct_multi_t* out, int count, const int64_t* sh
   }
   // Group by shape (largest transforms first, so that they start first);
   // a group holds at most 65535 transforms (one batched plan).
-  std::map<std::pair<int64_t, int64_t>, std::vector<int>> by_shape;
-  for (int i = 0; i < count; ++i) by_shape[{shapes[2 * i], shapes[2 * i + 1]}].push_back(i);
-  std::vector<std::pair<std::pair<int64_t, int64_t>, std::vector<int>>> order(by_shape.begin(), by_shape.end());
-  std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
-    return x.first.first * x.first.second > y.first.first * y.first.second;
-  });
-  m->offsets.assign(count, 0);
   int64_t off = 0;
+  const std::vector<LayoutGroup> layout = plan_layout(count, shapes, &m->offsets, &off);
   gbdct_status st = GBDCT_OK;
-  for (auto& kv : order) {
-    const int64_t n1 = kv.first.first, n2 = kv.first.second, sz = n1 * n2;
-    for (size_t b0 = 0; b0 < kv.second.size() && st == GBDCT_OK; b0 += 65535) {
-      const int64_t cnt = std::min<int64_t>(65535, (int64_t)kv.second.size() - (int64_t)b0);
-      Group g{n1, n2, cnt, off, nullptr};
-      const int64_t dims[2] = {n1, n2};
-      st = (flags & GBDCT_MULTI_TUNE) ? gbdct_plan_create_tuned(&g.plan, 2, dims, cnt, kind, GBDCT_F32, nullptr, 0)
-                                      : gbdct_plan_create_batched(&g.plan, 2, dims, cnt, kind, GBDCT_F32);
-      if (st != GBDCT_OK) break;
-      for (int64_t j = 0; j < cnt; ++j) m->offsets[kv.second[b0 + j]] = off + j * sz;
-      off += cnt * sz;
-      m->groups.push_back(g);
-    }
+  for (const LayoutGroup& lg : layout) {
+    const int64_t cnt = (int64_t)lg.members.size();
+    Group g{lg.n1, lg.n2, cnt, m->offsets[lg.members[0]], nullptr};
+    const int64_t dims[2] = {lg.n1, lg.n2};
+    st = (flags & GBDCT_MULTI_TUNE) ? gbdct_plan_create_tuned(&g.plan, 2, dims, cnt, kind, GBDCT_F32, nullptr, 0)
+                                    : gbdct_plan_create_batched(&g.plan, 2, dims, cnt, kind, GBDCT_F32);
     if (st != GBDCT_OK) break;
+    m->groups.push_back(g);
   }
   m->total = off;
   cudaError_t e = cudaSuccess;

@@ -104,3 +104,32 @@ def test_multi_and_family_rejections_before_touching_the_gpu(lib):
     assert lib.gbdct_plan_create_family(ctypes.byref(h), 2, dims, 1, 0, 0, None) == binding.ERR_INVALID_ARG
     assert lib.gbdct_plan_create_tuned(ctypes.byref(h), 2, dims, 0, 0, 0, None, 0) == binding.ERR_INVALID_ARG
     assert not h.value
+
+
+def test_multi_layout_is_a_dense_grouped_packing():
+    """The packed layout of an uneven batch, computed on the host: every
+    transform gets its own 16-byte-aligned range, the ranges tile the buffer
+    exactly, equal shapes are contiguous in index order, larger shapes first."""
+    from paper_2110_01172_gb300 import inputs
+    shapes = inputs.batched_shapes(512, seed=0, lo=64, hi=1024)
+    offs, total, groups = binding.multi_layout(shapes)
+    sizes = [a * b for a, b in shapes]
+    assert total == sum(sizes)
+    assert groups == len(set(shapes))
+    spans = sorted((o, o + s) for o, s in zip(offs, sizes))
+    assert spans[0][0] == 0 and spans[-1][1] == total
+    assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))       # no gap, no overlap
+    assert all(o % 4 == 0 for o in offs)                               # 16-byte aligned
+    by_shape = {}
+    for i, sh in enumerate(shapes):
+        by_shape.setdefault(sh, []).append(i)
+    starts = []
+    for sh, idx in by_shape.items():
+        o = [offs[i] for i in idx]
+        assert o == sorted(o)                                          # index order within a group
+        assert all(b - a == sh[0] * sh[1] for a, b in zip(o, o[1:]))  # contiguous batch
+        starts.append((o[0], sh[0] * sh[1]))
+    starts.sort()
+    assert [s for _, s in starts] == sorted((s for _, s in starts), reverse=True)   # largest first
+    with pytest.raises(ValueError):
+        binding.multi_layout([(64, 64), (96, 64)])
