@@ -417,6 +417,25 @@ def run_configs(dev, peak):
     for kind in ("dst2", "idct_idxst", "idxst_idct"):
         out["kinds_2048"].append(one((2048, 2048), kind))
 
+    # split-BF16 DFT-GEMM precision mode (tensor cores) beside the FP32 path
+    out["split_bf16"] = []
+    for shape, batch in (((1024, 1024), 1), ((256, 256), 64)):
+        p32 = Plan(shape, batch=batch)
+        pg = Plan(shape, batch=batch).set_precision("split_bf16")
+        full = ((batch,) if batch > 1 else ()) + shape
+        xs = [torch.rand(full, device=dev) * 2 - 1 for _ in range(2)]
+        ys = [torch.empty_like(xs[0]) for _ in range(2)]
+        rec = {"shape": list(shape), "batch": batch}
+        rec["fp32_fwd_us"] = _event_loop_us(lambda i: p32.forward(xs[i % 2], ys[i % 2]), 20, stream)
+        rec["split_bf16_fwd_us"] = _event_loop_us(lambda i: pg.forward(xs[i % 2], ys[i % 2]), 20, stream)
+        a, b = p32.forward(xs[0]), pg.forward(xs[0])
+        rec["rel_l2_vs_fp32_path"] = ((b - a).norm() / a.norm()).item()
+        flops = 3 * 2.0 * batch * shape[0] * shape[1] * (shape[0] + shape[1])
+        rec["split_bf16_tflops"] = flops / (rec["split_bf16_fwd_us"] * 1e-6) / 1e12
+        out["split_bf16"].append(rec)
+        p32.close()
+        pg.close()
+
     shapes = inputs.batched_shapes(512, seed=0, lo=64, hi=1024)
     rec = {"transforms": len(shapes), "sides": "log-uniform powers of two 64..1024, squares and 1:2 rectangles"}
     for graph in (True, False):

@@ -67,6 +67,11 @@ typedef enum gbdct_dtype {
   GBDCT_F32 = 0               /* float32 input and output, float32 arithmetic */
 } gbdct_dtype;
 
+typedef enum gbdct_precision {
+  GBDCT_PREC_FP32 = 0,        /* default: the FFT kernels, FP32 arithmetic */
+  GBDCT_PREC_SPLIT_BF16 = 1   /* dense DFT-GEMMs on the tensor cores, bf16 hi+lo split, FP32 accumulation */
+} gbdct_precision;
+
 /* Human-readable name of a status code (static storage, never NULL). */
 const char* gbdct_status_string(gbdct_status status);
 
@@ -183,6 +188,21 @@ gbdct_status gbdct_plan_create_family(gbdct_plan_t* out, int ndim, const int64_t
  */
 gbdct_status gbdct_plan_create_tuned(gbdct_plan_t* out, int ndim, const int64_t* dims, int64_t batch, int kind,
                                      int dtype, char* family_out, size_t family_cap);
+
+/*
+ * Precision mode of a plan.  GBDCT_PREC_SPLIT_BF16 evaluates the separable
+ * definition as dense products, X = C1 x C2^T forward and x = D1 X D2^T
+ * inverse (C the DCT-II matrix, D its exact inverse), on the tensor cores:
+ * every operand is split into bf16 hi + lo parts and each product is
+ * accumulated in FP32 as hi*hi + hi*lo + lo*hi.  Its error is that of the
+ * split (about 1e-5 relative in L2, stated per result), not the FP32 path's.
+ * Supported for 2D GBDCT_DCT2 plans with both sides <= 2048 (UNSUPPORTED
+ * otherwise); the first switch allocates the matrices (FP64-generated, split
+ * once) and 2 bf16 + 1 FP32 arrays of batch*N1*N2 and synchronises the device.
+ * gbdct_exec_step is UNSUPPORTED in this mode.  GBDCT_PREC_FP32 switches back.
+ * Errors: INVALID_ARG (NULL plan, unknown mode), UNSUPPORTED, OOM, CUDA.
+ */
+gbdct_status gbdct_plan_set_precision(gbdct_plan_t plan, int precision);
 
 /*
  * Uneven-size batches of 2D transforms (the batch parallelism of Section IV:

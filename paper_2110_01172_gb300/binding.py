@@ -85,6 +85,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_poisson_destroy": (ctypes.c_int, [plan_p]),
             "gbdct_dct2d_forward_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                            ctypes.c_int64, ctypes.c_void_p]),
+            "gbdct_plan_set_precision": (ctypes.c_int, [plan_p, ctypes.c_int]),
             "gbdct_plan_create_family": (ctypes.c_int, [ctypes.POINTER(plan_p), ctypes.c_int, c_i64p,
                                                         ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                                         ctypes.c_char_p]),
@@ -170,6 +171,15 @@ class Plan:
     @property
     def workspace_bytes(self) -> int:
         return int(self._lib.gbdct_plan_workspace_bytes(self._h))
+
+    def set_precision(self, precision: str):
+        """"fp32" (the FFT kernels) or "split_bf16" (tensor-core DFT-GEMMs, ~1e-5 error)."""
+        modes = {"fp32": 0, "split_bf16": 1}
+        if precision not in modes:
+            raise ValueError(f"unknown precision {precision!r}")
+        with _torch().cuda.device(self.device):
+            _check(self._lib.gbdct_plan_set_precision(self._h, modes[precision]), "gbdct_plan_set_precision")
+        return self
 
     @property
     def family(self) -> str:

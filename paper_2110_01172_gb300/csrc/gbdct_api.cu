@@ -9,6 +9,7 @@
 #include "../../include/gbdct.h"
 #include "dct2d_launch.cuh"
 #include "dct_axis0.cuh"
+#include "gemm_path.cuh"
 
 using gbdct::Dct2dArgs;
 
@@ -39,6 +40,8 @@ struct gbdct_plan_s {
   const float2* ax_iw; // e^{+i pi k / 2 N0} / N0
   gbdct::AxisArgs ax;  // axis-0 pass arguments (in, out, w set per call)
   int lg0;
+  int precision;             // GBDCT_PREC_FP32 (FFT kernels) or GBDCT_PREC_SPLIT_BF16
+  gbdct::GemmPath* gemm;     // split-BF16 DFT-GEMM state (precision mode only)
 };
 
 namespace {
@@ -202,6 +205,7 @@ bool device_accessible(const void* ptr, int device, cudaStream_t s) {
 void free_plan(gbdct_plan_s* p) {
   if (!p) return;
   if (p->inner) gbdct_plan_destroy(p->inner);
+  if (p->gemm) gbdct::gemm_destroy(p->gemm);
   if (p->ax_tables) cudaFree(p->ax_tables);
   if (p->tables) cudaFree(p->tables);
   if (p->work) cudaFree(p->work);
@@ -546,6 +550,9 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!device_accessible(in, p->device, s) || !device_accessible(out, p->device, s)) return GBDCT_ERR_INVALID_ARG;
   if (p->ndim == 3) return exec3d(p, in, out, s, inverse, step);
+  if (p->precision == GBDCT_PREC_SPLIT_BF16)
+    return step >= 0 ? GBDCT_ERR_UNSUPPORTED
+                     : gbdct::gemm_exec(p->gemm, inverse, static_cast<const float*>(in), static_cast<float*>(out), s);
   if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse, step);
   if (!inverse && (p->kind == GBDCT_IDCT_IDXST || p->kind == GBDCT_IDXST_IDCT)) return GBDCT_ERR_UNSUPPORTED;
   if (p->family == FAM_FS2) return exec_core(p, in, out, s, inverse, step);  // maps folded in (vkind)
@@ -677,10 +684,33 @@ const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step) {
   return inverse ? kInv2[k] : kFwd2[k];
 }
 
-size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) { return plan ? plan->work_bytes : 0; }
+size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) {
+  return plan ? plan->work_bytes + gbdct::gemm_workspace_bytes(plan->gemm) : 0;
+}
+
+gbdct_status gbdct_plan_set_precision(gbdct_plan_t plan, int precision) {
+  if (!plan) return GBDCT_ERR_INVALID_ARG;
+  if (precision == GBDCT_PREC_FP32) {
+    plan->precision = GBDCT_PREC_FP32;  // the DFT-GEMM state is kept for a later switch back
+    return GBDCT_OK;
+  }
+  if (precision != GBDCT_PREC_SPLIT_BF16) return GBDCT_ERR_INVALID_ARG;
+  if (plan->ndim != 2 || plan->kind != GBDCT_DCT2) return GBDCT_ERR_UNSUPPORTED;
+  if (plan->n1 > gbdct::kGemmMaxSide || plan->n2 > gbdct::kGemmMaxSide || plan->batch > 65535)
+    return GBDCT_ERR_UNSUPPORTED;
+  if (!plan->gemm) {
+    DeviceGuard guard(plan->device);
+    gbdct_status st = GBDCT_OK;
+    plan->gemm = gbdct::gemm_create(plan->n1, plan->n2, (int)plan->batch, &st);
+    if (!plan->gemm) return st;
+  }
+  plan->precision = GBDCT_PREC_SPLIT_BF16;
+  return GBDCT_OK;
+}
 
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (!plan) return 0;
+  if (plan->precision == GBDCT_PREC_SPLIT_BF16) return 8;  // 2 split kernels + 6 GEMMs (library launches may add more)
   if (plan->ndim == 3) return gbdct_plan_launches_per_exec(plan->inner) + 1;
   const int core = core_launches(plan);
   return (plan->kind == GBDCT_DCT2 || plan->family == FAM_FS2) ? core : core + 2;
