@@ -9,8 +9,11 @@
  * mirror image: the four-reads/two-writes twiddle preprocess (Eq. 2d_idct_pre),
  * a complex-to-real 2D FFT and the inverse reorder (Eq. 2d_idct_post).  The
  * reorder and the twiddle stages are fused into the first and last FFT passes,
- * so a transform is two kernel launches and one on-chip/L2-resident
- * intermediate.
+ * so a 2D transform is two or three kernel launches (by kernel family; three
+ * for the default four-step family) around one L2-resident intermediate.  The
+ * same plans cover batches, 3D (Section III-D), the DST-II / IDXST kinds of
+ * Section V-B, uneven-size batches, the spectral Poisson solve of Algorithm 4
+ * and a split-BF16 tensor-core precision mode.
  *
  * Conventions (all arrays are dense, row-major, last axis contiguous):
  *   forward  X[k1,k2] = sum_{n1,n2} x[n1,n2] cos(pi k1 (2n1+1)/(2N1))
@@ -21,7 +24,8 @@
  *            so inverse(forward(x)) == x.
  *
  * Every function returns a gbdct_status; no C++ exception crosses the ABI.
- * Pointers named "device" must point to memory of the plan's CUDA device.
+ * Pointers named "device" must point to memory of the plan's CUDA device;
+ * the exec calls also accept page-locked host buffers (see gbdct_exec_forward).
  * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  * A plan may be used by one stream at a time (it owns one workspace).
  */
@@ -150,7 +154,10 @@ int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
  * NULL plan).  Every family computes the same transform; the plan picks the
  * fastest one that supports the shape, and the environment variable
  * GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp|fs2, read at plan creation, forces a family
- * when it supports the shape (for testing and comparison). */
+ * when it supports the shape (for testing and comparison).  Within fs2,
+ * GBDCT_FS2_COLS=scalar selects the one-column-per-thread column steps and
+ * GBDCT_FS2_ROWS=persistent the persistent, bulk-copy-prefetching row passes
+ * (both measured slower than the defaults). */
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
 
 /* Reports (and clears) a failure recorded on the device by the plan's
