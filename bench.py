@@ -48,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 # from the ncu capture summarised in profiles/, valid only for the kernel
 # sources with this digest (otherwise reported as null).
 TRAFFIC = {
-    "sources_sha256": "486108fabd254ea208ae9fe23ae8ee4da1af0811d04fbaf102aff625a15d2e16",
+    "sources_sha256": "e21be0e8c0b4c89e9cb05710326dc65804da77e7f8bf6c30b05911be9a6dab61",
     "family": "fs2",
     "bytes_per_launch": {   # profiles/fs2_kernels_4096_ncu.md (cold L2 under ncu)
         "forward column step C1 (reorder + DFT_B + twiddle)": 67166720 + 18386432,

@@ -5,17 +5,21 @@
 // length N1 = A*B split the four-step way so that every global access is a
 // contiguous row segment), with kernels shaped for occupancy:
 //
-//  * column steps: a CTA owns a slab of S rows (S = A or B) x 128 complex
-//    columns and 512 threads; the four threads of a column each hold T = S/4
-//    points, so a DFT_S is a DFT_T in registers, a twiddle W_S^{q m}, an
-//    exchange through shared memory and DFT4s (S = 4T:
-//    W_S^{(q+4j)(m+Tp)} = W_S^{qm} W_4^{qp} W_T^{jm});
+//  * column steps: a CTA owns a slab of S rows (S = A or B) x a block of
+//    complex columns; Q threads share a column group and each holds T = S/Q
+//    points of it, so a DFT_S is a DFT_T in registers, a twiddle W_S^{q m},
+//    an exchange through shared memory and DFT_Qs
+//    (W_S^{(q+Qj)(m+Tp)} = W_S^{qm} W_Q^{qp} W_T^{jm}).  The default vector
+//    form (k_fs2_colv) gives each thread two adjacent columns (16-byte
+//    accesses; Q = 4 or 8, S up to 128); the scalar form (k_fs2_col) one
+//    column with Q = 4;
 //  * row passes: one sequence per 16-point thread group (float2), the radix-16
 //    Stockham engine of fft_core.cuh, ~64 registers per thread.
 //
 // Workspace layout as in dct2d_fs_kernels.cuh: N1 rows of N2/2 complex, row
 // k1 of the column spectrum at physical row (k1 % B) * A + k1 / B.
-// Supported: N1 in {256, ..., 4096}, N2 in {256, ..., 16384}.
+// Supported: N1 in {256, ..., 8192} (8192 with the vector column steps only),
+// N2 in {256, ..., 16384}.
 //
 // The other kinds are index/sign maps around the DCT-II (Section V-B, Eq.
 // idxst; DST-II per axis), folded into the first loads and last stores
