@@ -133,3 +133,14 @@ def test_multi_layout_is_a_dense_grouped_packing():
     assert [s for _, s in starts] == sorted((s for _, s in starts), reverse=True)   # largest first
     with pytest.raises(ValueError):
         binding.multi_layout([(64, 64), (96, 64)])
+
+
+def test_precision_and_layout_null_paths(lib):
+    assert lib.gbdct_plan_set_precision(None, 1) == binding.ERR_INVALID_ARG
+    assert lib.gbdct_plan_set_precision(None, 0) == binding.ERR_INVALID_ARG
+    shapes = (ctypes.c_int64 * 2)(64, 64)
+    assert lib.gbdct_multi_layout(0, shapes, None, None) == -1
+    assert lib.gbdct_multi_layout(1, None, None, None) == -1
+    assert lib.gbdct_multi_layout(1, shapes, None, None) == 64 * 64
+    bad = (ctypes.c_int64 * 2)(64, 65)
+    assert lib.gbdct_multi_layout(1, bad, None, None) == -1
