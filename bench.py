@@ -235,7 +235,7 @@ def cpu_baseline(n1: int, n2: int, steps: int = 6):
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": f"failed: {e}"}
     return {"value": step_s * 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} full steps (FP64 separable direct-sum DCT-II + inverse, {n1}x{n2}; '10 s of CPU work), best"}
+            "sample": f"{steps} full steps (FP64 separable direct-sum DCT-II + inverse, {n1}x{n2}; about 10 s of CPU work), best"}
 
 
 # ---------------------------------------------------------------------------
