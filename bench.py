@@ -345,8 +345,11 @@ def run_baselines(dev, n1, n2, ours_fwd_us, ours_inv_us, peak):
     ys = [torch.empty_like(xs[0]) for _ in range(2)]
     out = {}
     h1, h2 = ctypes.c_void_p(), ctypes.c_void_p()
-    if lib.gbdct_b1_create(ctypes.byref(h1), n1, n2) != 0 or lib.gbdct_b2_create(ctypes.byref(h2), n1, n2) != 0:
-        return {"unavailable": "baseline plan creation failed"}
+    if lib.gbdct_b1_create(ctypes.byref(h1), n1, n2) != 0:
+        return {"unavailable": "baseline B1 plan creation failed"}
+    if lib.gbdct_b2_create(ctypes.byref(h2), n1, n2) != 0:
+        lib.gbdct_b1_destroy(h1)
+        return {"unavailable": "baseline B2 plan creation failed"}
     ptr = lambda t: ctypes.c_void_p(t.data_ptr())
     b1f = _event_loop_us(lambda i: lib.gbdct_b1_forward(h1, ptr(xs[i % 2]), ptr(ys[i % 2]), sp), 20, stream)
     b1i = _event_loop_us(lambda i: lib.gbdct_b1_inverse(h1, ptr(ys[i % 2]), ptr(xs[i % 2]), sp), 20, stream)

@@ -124,6 +124,7 @@ __global__ void k_b2_post_t(const float2* __restrict__ W, float* __restrict__ Y,
 struct gbdct_b1_s {
   int n1, n2;
   cufftHandle r2c, c2r;
+  bool has_r2c = false, has_c2r = false;
   float* v;
   float2* V;
   float2 *a, *b;  // a: n1 entries, b: n2 entries
@@ -132,6 +133,7 @@ struct gbdct_b1_s {
 struct gbdct_b2_s {
   int n1, n2;
   cufftHandle rows1, rows2;  // batched 1D R2C: n1 rows of n2, then n2 rows of n1
+  bool has_rows1 = false, has_rows2 = false;
   float *v, *y;
   float2* W;
   float2 *a, *b;
@@ -139,13 +141,20 @@ struct gbdct_b2_s {
 
 extern "C" {
 
+int gbdct_b1_destroy(gbdct_b1_s* p);
+int gbdct_b2_destroy(gbdct_b2_s* p);
+
 int gbdct_b1_create(gbdct_b1_s** out, int n1, int n2) {
   gbdct_b1_s* p = new (std::nothrow) gbdct_b1_s();
   if (!p) return -1;
   p->n1 = n1;
   p->n2 = n2;
   int st = cufftPlan2d(&p->r2c, n1, n2, CUFFT_R2C);
-  if (!st) st = cufftPlan2d(&p->c2r, n1, n2, CUFFT_C2R);
+  p->has_r2c = !st;
+  if (!st) {
+    st = cufftPlan2d(&p->c2r, n1, n2, CUFFT_C2R);
+    p->has_c2r = !st;
+  }
   cudaError_t e = cudaSuccess;
   if (!st) e = cudaMalloc(&p->v, sizeof(float) * n1 * n2);
   if (!st && !e) e = cudaMalloc(&p->V, sizeof(float2) * n1 * (n2 / 2 + 1));
@@ -156,8 +165,13 @@ int gbdct_b1_create(gbdct_b1_s** out, int n1, int n2) {
     k_tw<<<(n2 + 255) / 256, 256>>>(p->b, n2, n2);
     e = cudaDeviceSynchronize();
   }
+  if (st || e) {
+    gbdct_b1_destroy(p);
+    *out = nullptr;
+    return st ? st : (int)e;
+  }
   *out = p;
-  return st ? st : (int)e;
+  return 0;
 }
 
 int gbdct_b1_forward(gbdct_b1_s* p, const float* x, float* X, void* stream) {
@@ -182,8 +196,8 @@ int gbdct_b1_inverse(gbdct_b1_s* p, const float* C, float* x, void* stream) {
 
 int gbdct_b1_destroy(gbdct_b1_s* p) {
   if (!p) return 0;
-  cufftDestroy(p->r2c);
-  cufftDestroy(p->c2r);
+  if (p->has_r2c) cufftDestroy(p->r2c);
+  if (p->has_c2r) cufftDestroy(p->c2r);
   cudaFree(p->v);
   cudaFree(p->V);
   cudaFree(p->a);
@@ -199,7 +213,11 @@ int gbdct_b2_create(gbdct_b2_s** out, int n1, int n2) {
   p->n2 = n2;
   int len2 = n2, len1 = n1;
   int st = cufftPlanMany(&p->rows1, 1, &len2, nullptr, 1, n2, nullptr, 1, n2 / 2 + 1, CUFFT_R2C, n1);
-  if (!st) st = cufftPlanMany(&p->rows2, 1, &len1, nullptr, 1, n1, nullptr, 1, n1 / 2 + 1, CUFFT_R2C, n2);
+  p->has_rows1 = !st;
+  if (!st) {
+    st = cufftPlanMany(&p->rows2, 1, &len1, nullptr, 1, n1, nullptr, 1, n1 / 2 + 1, CUFFT_R2C, n2);
+    p->has_rows2 = !st;
+  }
   cudaError_t e = cudaSuccess;
   const size_t hw = (size_t)n1 * (n2 / 2 + 1) > (size_t)n2 * (n1 / 2 + 1) ? (size_t)n1 * (n2 / 2 + 1)
                                                                             : (size_t)n2 * (n1 / 2 + 1);
@@ -213,8 +231,13 @@ int gbdct_b2_create(gbdct_b2_s** out, int n1, int n2) {
     k_tw<<<(n2 + 255) / 256, 256>>>(p->b, n2, n2);
     e = cudaDeviceSynchronize();
   }
+  if (st || e) {
+    gbdct_b2_destroy(p);
+    *out = nullptr;
+    return st ? st : (int)e;
+  }
   *out = p;
-  return st ? st : (int)e;
+  return 0;
 }
 
 int gbdct_b2_forward(gbdct_b2_s* p, const float* x, float* X, void* stream) {
@@ -236,8 +259,8 @@ int gbdct_b2_forward(gbdct_b2_s* p, const float* x, float* X, void* stream) {
 
 int gbdct_b2_destroy(gbdct_b2_s* p) {
   if (!p) return 0;
-  cufftDestroy(p->rows1);
-  cufftDestroy(p->rows2);
+  if (p->has_rows1) cufftDestroy(p->rows1);
+  if (p->has_rows2) cufftDestroy(p->rows2);
   cudaFree(p->v);
   cudaFree(p->y);
   cudaFree(p->W);
