@@ -150,14 +150,13 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan);
 /* Number of kernel launches one exec call issues (0 for a NULL plan). */
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
 
-/* Name of the kernel family the plan runs ("seq", "pair", "r64", "fs", "fsp" or "fs2"; "" for a
+/* Name of the kernel family the plan runs ("seq", "pair" or "fs2"; "" for a
  * NULL plan).  Every family computes the same transform; the plan picks the
- * fastest one that supports the shape, and the environment variable
- * GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp|fs2, read at plan creation, forces a family
- * when it supports the shape (for testing and comparison).  Within fs2,
- * GBDCT_FS2_COLS=scalar selects the one-column-per-thread column steps and
- * GBDCT_FS2_ROWS=persistent the persistent, bulk-copy-prefetching row passes
- * (both measured slower than the defaults). */
+ * fastest one that supports the shape (fs2: N1 in 256..8192 and N2 in
+ * 256..16384; pair: both sides in 16..8192; seq: any supported size), and the
+ * environment variable GBDCT_KERNEL_FAMILY=seq|pair|fs2, read at plan
+ * creation, forces a family when it supports the shape (for testing and
+ * comparison). */
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
 
 /* Reports (and clears) a failure recorded on the device by the plan's
@@ -174,7 +173,7 @@ gbdct_status gbdct_plan_destroy(gbdct_plan_t plan);
 
 /*
  * As gbdct_plan_create_batched with the kernel family named by `family`
- * ("seq", "pair", "r64", "fs", "fsp" or "fs2"; every family computes the same
+ * ("seq", "pair" or "fs2"; every family computes the same
  * transform).  Errors: INVALID_ARG (NULL or unknown name, and the checks of
  * gbdct_plan_create_batched), UNSUPPORTED when that family does not support
  * the shape, OOM, CUDA.  For a 3D plan the family applies to its 2D slices.

@@ -144,7 +144,7 @@ class Plan:
 
     def __init__(self, shape, kind: str = "dct2", batch: int = 1, device=None, family: str | None = None,
                  tuned: bool = False):
-        """family: force a kernel family ("seq", "pair", "r64", "fs", "fsp", "fs2");
+        """family: force a kernel family ("seq", "pair", "fs2");
         tuned: pick the fastest family by timing (gbdct_plan_create_tuned)."""
         torch = _torch()
         lib = load()

@@ -35,15 +35,20 @@
 #pragma once
 
 #include "dct2d_kernels.cuh"
-#include "fft_r64.cuh"
-#include "pipe.cuh"
+#include "fft_soa.cuh"
 
 #include <type_traits>
 
 namespace gbdct {
 
-constexpr int kCsCols = 128;            // complex columns per column-step CTA
-constexpr int kCsThreads = 4 * kCsCols;  // four threads per column
+// Calls f(integral_constant<int, I>) for I = B .. E-1 (compile-time loop).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
 
 template <int N1>
 struct Fs2Geom {
@@ -53,125 +58,6 @@ struct Fs2Geom {
 
 // Physical workspace row of column-spectrum row k1 (A, B powers of two).
 __device__ __forceinline__ int fs2_prow(int k1, int A, int B) { return (k1 & (B - 1)) * A + k1 / B; }
-
-// Multiplies X[m] (m < T) by W_S^{q m} for the thread's runtime q in [0, 4)
-// (q is uniform across a warp, so the switch does not diverge).
-template <int S, bool INV>
-__device__ __forceinline__ void cs_twiddle(float2* X, int q) {
-  constexpr int T = S / 4;
-  switch (q) {
-    case 1: r64::static_for<1, T>([&](auto mc) { constexpr int m = decltype(mc)::value; X[m] = r64::mul_w<S, 1 * m, INV>(X[m]); }); break;
-    case 2: r64::static_for<1, T>([&](auto mc) { constexpr int m = decltype(mc)::value; X[m] = r64::mul_w<S, 2 * m, INV>(X[m]); }); break;
-    case 3: r64::static_for<1, T>([&](auto mc) { constexpr int m = decltype(mc)::value; X[m] = r64::mul_w<S, 3 * m, INV>(X[m]); }); break;
-    default: break;
-  }
-}
-
-// DFT_S along the slab rows for the thread's column: on entry x[j] = row q + 4j
-// (j < T); on return y[i * 4 + p] = output row (q*T/4 + i) + T p  (i < T/4, p < 4).
-// `ex` is the CTA's S x 128 exchange buffer; contains one __syncthreads pair.
-template <int S, bool INV>
-__device__ __forceinline__ void cs_dft(float2* x, int q, int c, float2* ex) {
-  constexpr int T = S / 4;
-  r64::dft<T, INV>(x);
-  cs_twiddle<S, INV>(x, q);
-#pragma unroll
-  for (int m = 0; m < T; ++m) ex[(q * T + m) * kCsCols + c] = x[m];
-  __syncthreads();
-  constexpr int TQ = T / 4;  // m values per thread
-#pragma unroll
-  for (int i = 0; i < TQ; ++i) {
-    const int m = q * TQ + i;
-    float2 a0 = ex[(0 * T + m) * kCsCols + c], a1 = ex[(1 * T + m) * kCsCols + c];
-    float2 a2 = ex[(2 * T + m) * kCsCols + c], a3 = ex[(3 * T + m) * kCsCols + c];
-    dft4<INV>(a0, a1, a2, a3);
-    x[i * 4 + 0] = a0;
-    x[i * 4 + 1] = a1;
-    x[i * 4 + 2] = a2;
-    x[i * 4 + 3] = a3;
-  }
-  __syncthreads();
-}
-
-// Output slab row of register y[i*4 + p] (see cs_dft).
-template <int S>
-__device__ __forceinline__ int cs_out_row(int q, int i, int p) {
-  return q * (S / 16) + i + (S / 4) * p;
-}
-
-// ----------------------------------------------------------------------------
-// Column steps.  KIND 0: forward C1 (x rows -> DFT_B -> W_N1 twiddle)
-//                KIND 1: forward C2 (DFT_A in place)
-//                KIND 2: inverse C2' (IDFT_A, conj W_N1 twiddle, in place)
-//                KIND 3: inverse C1' (IDFT_B -> output rows, inverse reorder)
-// blockIdx.x = slab (n1a for KIND 0/3, k1b for KIND 1/2), blockIdx.y = column
-// block, blockIdx.z = batch.
-// ----------------------------------------------------------------------------
-template <int N1, int KIND>
-__global__ void __launch_bounds__(kCsThreads, 2)
-k_fs2_col(Dct2dArgs a) {
-  using G = Fs2Geom<N1>;
-  constexpr bool INV = KIND >= 2;
-  constexpr int S = (KIND == 0 || KIND == 3) ? G::B : G::A;
-  constexpr int T = S / 4;
-  extern __shared__ float4 scs[];
-  float2* ex = reinterpret_cast<float2*>(scs);
-  const int c = threadIdx.x % kCsCols, q = threadIdx.x / kCsCols;
-  const int r = blockIdx.x, cb = blockIdx.y;
-  const int N2 = a.n2;
-  const long long half = N2 / 2;  // complex per workspace row
-  const int col = cb * kCsCols + c;
-  float2* W = a.work + (long long)blockIdx.z * a.work_bstride;
-
-  float2 x[T];
-#pragma unroll
-  for (int j = 0; j < T; ++j) {
-    const int i = q + 4 * j;  // slab row of this input
-    const float2* src;
-    if constexpr (KIND == 0) {
-      const float* xin = a.in + (long long)blockIdx.z * a.in_bstride;
-      const int row = reorder_src(r + G::A * i, N1);
-      src = reinterpret_cast<const float2*>(xin + (long long)row * N2) + col;
-      x[j] = *src;
-      if (a.vkind == 1) {  // DST-II: (-1)^(n1 + n2) on columns 2 col, 2 col + 1
-        const float sr = (row & 1) ? -1.f : 1.f;
-        x[j] = make_float2(sr * x[j].x, -sr * x[j].y);
-      }
-      continue;
-    } else if constexpr (KIND == 3) {
-      src = W + (long long)(i * G::A + r) * half + col;
-    } else {
-      src = W + (long long)(r * G::A + i) * half + col;
-    }
-    x[j] = *src;
-  }
-  cs_dft<S, INV>(x, q, c, ex);
-#pragma unroll
-  for (int i = 0; i < T / 4; ++i)
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int o = cs_out_row<S>(q, i, p);  // k1b (KIND 0), k1a (1), n1a (2), n1b (3)
-      float2 y = x[i * 4 + p];
-      if constexpr (KIND == 0) {
-        y = cmul(y, __ldg(a.fstw + r * G::B + o));
-        W[(long long)(o * G::A + r) * half + col] = y;
-      } else if constexpr (KIND == 2) {
-        y = cmulc(y, __ldg(a.fstw + o * G::B + r));
-        W[(long long)(r * G::A + o) * half + col] = y;
-      } else if constexpr (KIND == 1) {
-        W[(long long)(r * G::A + o) * half + col] = y;
-      } else {
-        float* xo = a.out + (long long)blockIdx.z * a.out_bstride;
-        const int row = reorder_src(r + G::A * o, N1);
-        if (a.vkind) {  // output signs: (-1)^(n1+n2) DST-II, (-1)^n2 IDCT_IDXST, (-1)^n1 IDXST_IDCT
-          const float sr = (a.vkind != 2 && (row & 1)) ? -1.f : 1.f;
-          const float sc = (a.vkind != 3) ? -sr : sr;
-          y = make_float2(sr * y.x, sc * y.y);
-        }
-        *(reinterpret_cast<float2*>(xo + (long long)row * N2) + col) = y;
-      }
-    }
-}
 
 // ----------------------------------------------------------------------------
 // Column steps, vector form (k_fs2_colv): each thread owns CPT adjacent complex
@@ -355,10 +241,10 @@ struct ColCfg {
 // x[m] *= W_S^{q m} (m < T) for the thread's warp-uniform q < Q.
 template <int S, int Q, int T, bool INV, typename V>
 __device__ __forceinline__ void colv_twiddle(V* x, int q) {
-  r64::static_for<1, Q>([&](auto qc) {
+  static_for<1, Q>([&](auto qc) {
     constexpr int qq = decltype(qc)::value;
     if (q == qq) {
-      r64::static_for<1, T>([&](auto mc) {
+      static_for<1, T>([&](auto mc) {
         constexpr int m = decltype(mc)::value;
         x[m] = mul_w128<S, qq * m, INV>(x[m]);
       });
@@ -467,10 +353,8 @@ k_fs2_colv(Dct2dArgs a) {
 // Eqs. four-elements, s-t) -> output rows k1 and N1-k1.  Inverse: four-read
 // preprocess (Eq. 2d_idct_pre, conjugated twiddle, 1/(N1 N2) in the a-table),
 // row IFFT, column pairing Z_p(k1) = U(k1,p) + i U(k1,L-1-p) -> workspace.
-// Two variants share the arithmetic: one item group per CTA with the rows
-// staged by the threads (k_fs2_*_rows), and persistent CTAs that prefetch the
-// next item's rows with bulk copies while computing the current one
-// (k_fs2p_rows).
+// One item group per CTA with the rows staged by the threads (k_fs2_rows);
+// used for N2 = 16384, where the two-item form below does not fit.
 // ----------------------------------------------------------------------------
 template <int L>
 struct RowGeom {
@@ -480,11 +364,6 @@ struct RowGeom {
   static constexpr int LP = pad_len<float2>(L);
   static constexpr size_t SMEM = (size_t)NI * LP * sizeof(float2);
   static constexpr int MINB = 1024 / THREADS;  // caps registers at 64 per thread
-  static constexpr size_t STAGE = (size_t)NI * 2 * L * sizeof(float);  // raw rows of the persistent variant
-  static constexpr size_t PSMEM = STAGE + SMEM + 16;                  // + mbarrier
-  // persistent CTAs per SM that shared memory allows (registers bounded to match)
-  static constexpr int PMINB_SMEM = (int)((227 * 1024) / PSMEM);
-  static constexpr int PMINB = PMINB_SMEM < 1 ? 1 : (PMINB_SMEM < MINB ? PMINB_SMEM : MINB);
 };
 
 __device__ __forceinline__ int row_mirror(int k1, int N1) { return k1 ? N1 - k1 : N1 / 2; }
@@ -761,95 +640,280 @@ __global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::MINB) k_fs2_r
   row_item<L, INV>(a, blockIdx.z, k1, reinterpret_cast<const float*>(s), s, g, ra == nullptr);
 }
 
-// Persistent variant: CTA c takes item groups c, c + grid, ...; while it
-// computes one group, the next group's rows (2 NI rows of 4L bytes) arrive by
-// bulk copy in a separate staging buffer.  Every wait is bounded; a wait that
-// gives up sets the device error word, and the CTA waits (bounded) for the
-// copy it issued before it returns.
-template <int L, bool INV>
-__global__ void __launch_bounds__(RowGeom<L>::THREADS, RowGeom<L>::PMINB) k_fs2p_rows(Dct2dArgs a, int batch) {
-  using R = RowGeom<L>;
-  extern __shared__ __align__(128) unsigned char prw[];
-  float* stage = reinterpret_cast<float*>(prw);
-  float2* fbuf = reinterpret_cast<float2*>(prw + R::STAGE);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(prw + R::STAGE + R::SMEM);
-  const int li = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
-  const int upb = a.n1 / 2 / R::NI;  // item groups per batch entry
-  const int nunits = upb * batch;
-  const int nk = (int)blockIdx.x < nunits ? (nunits - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  int issued = 0;  // thread 0: groups whose loads were issued
 
-  auto issue = [&](int k) {  // thread 0
-    const int u = blockIdx.x + k * gridDim.x;
-    const int b = u / upb, k0 = (u % upb) * R::NI;
-    uint32_t bytes = 0;
-    for (int i = 0; i < R::NI; ++i) {
-      const float *ra, *rb;
-      row_sources<L, INV>(a, b, k0 + i, &ra, &rb);
-      bytes += (ra ? 2u : 1u) * 4u * L;
+// ----------------------------------------------------------------------------
+// Row passes, two-item form (N2 <= 8192, the default).  A thread group of
+// L/16 threads transforms two row items at once in packed two-lane FP32
+// arithmetic (fft_soa.cuh): lane a is item k1, lane b item k1 + 1.  The
+// forward Hermitian split is fused into the loads (each thread reads its 16
+// points of the four column-spectrum rows straight from the workspace, no
+// staging copy), and the split's factor 1/2 is folded into the a-twiddle of
+// the combine.  The inverse reads its four-read preprocess inputs straight
+// from the input rows.  Item 0 (the packed rows 0 and N1/2) takes the
+// packed formulas in lane a of the first group.
+// ----------------------------------------------------------------------------
+template <int L>
+struct RowX2Geom {
+  static constexpr int TPS = fft_tps(L);                          // threads per item pair
+  static constexpr int NP = (256 / TPS) > 0 ? 256 / TPS : 1;      // item pairs per CTA
+  static constexpr int THREADS = NP * TPS;
+  static constexpr int LP = L + L / 16;                           // padded float4 per item pair
+  static constexpr size_t SMEM = (size_t)NP * LP * sizeof(float4);
+  static constexpr int MINB = THREADS >= 512 ? 1 : 3;      // forward: CTAs per SM (80 registers)
+  static constexpr int MINB_INV = THREADS >= 512 ? 1 : 2;  // inverse (its preprocess needs more)
+};
+
+// Column-spectrum rows of item k (row k1 and its mirror) in the workspace.
+template <int L>
+__device__ __forceinline__ void fwd_rows_of(const Dct2dArgs& a, const float2* Zw, int k, const float2** z,
+                                            const float2** m) {
+  *z = Zw + (long long)fs2_prow(k, a.fsA, a.fsB) * (L / 2);
+  *m = Zw + (long long)fs2_prow(row_mirror(k, a.n1), a.fsA, a.fsB) * (L / 2);
+}
+
+// First-stage butterfly of thread g of a group of TPS threads, arranged so that
+// the butterfly t and its mirror TPS-1-t sit in lanes l and l^m of one warp
+// (m = 16, or 15 when a warp holds two 16-thread groups).
+template <int TPS>
+__device__ __forceinline__ int mirror_lane_butterfly(int g) {
+  if constexpr (TPS >= 32) {
+    const int w = g >> 5, l = g & 31;
+    return l < 16 ? 16 * w + l : TPS + 15 - 16 * w - l;
+  } else {
+    return g;
+  }
+}
+template <int TPS>
+constexpr int mirror_lane_mask() { return TPS >= 32 ? 16 : TPS - 1; }
+
+// Forward split of two items from the workspace into SoA registers: point
+// n2 = t + TPS j of u = V_col(k1, :) is (z(p) + conj m(p)) / 2 for n2 < L/2
+// (p = n2) and (z(p) - conj m(p)) / 2i above (p = L-1-n2); the 1/2 is left out
+// here.  Packed lane a (item 0): u = V_col(0, :) + i V_col(N1/2, :).  Each
+// workspace value is read once: the thread reads its low-half points, forms
+// both the low value and the high value it implies (for point L-1-n2, which
+// belongs to the mirror butterfly TPS-1-t at j' = 15 - j), and the two mirror
+// lanes swap the high values.
+template <int L>
+__device__ __forceinline__ void fwd_split_x2(const float2* __restrict__ za, const float2* __restrict__ ma,
+                                             const float2* __restrict__ zb, const float2* __restrict__ mb, int t,
+                                             bool packed, soa::C2* v) {
+  constexpr int TPS = fft_tps(L);
+  constexpr int MASK = mirror_lane_mask<TPS>();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = t + TPS * j;
+    const float2 A = za[p], Am = ma[p], B = zb[p], Bm = mb[p];
+    // low point n2 = p (this thread), high point L-1-p (the mirror lane)
+    const float lra = packed ? A.x : A.x + Am.x, lia = packed ? Am.x : A.y - Am.y;
+    const float hra = packed ? A.y : A.y + Am.y, hia = packed ? Am.y : Am.x - A.x;
+    v[j] = soa::C2{make_float2(lra, B.x + Bm.x), make_float2(lia, B.y - Bm.y)};
+    const float h0 = hra, h1 = B.y + Bm.y, h2 = hia, h3 = Bm.x - B.x;
+    v[15 - j] = soa::C2{make_float2(__shfl_xor_sync(0xffffffffu, h0, MASK), __shfl_xor_sync(0xffffffffu, h1, MASK)),
+                        make_float2(__shfl_xor_sync(0xffffffffu, h2, MASK), __shfl_xor_sync(0xffffffffu, h3, MASK))};
+  }
+}
+
+// Forward combine (Section III-B, Eqs. four-elements / s-t) of both items from
+// the row spectra Y in s, one column pair (c, L-c) per thread and iteration:
+// u = aP + conj(aM), w = aP - conj(aM) (P = Y(c), M = Y(L-c)); with s = b u,
+// t = b w (b/2 in the table): y(k1,c) = Re s, y(kmir,c) = -Im t,
+// y(k1,L-c) = -Im s, y(kmir,L-c) = -Re t.  Packed lane a: a = 1 for row 0
+// and w = sqrt(1/2) (M.x - P.x, -(P.y + M.y)) for row N1/2.
+template <int L>
+__device__ __forceinline__ void fwd_post_x2(const float4* __restrict__ s, const Dct2dArgs& a, float* y, int k1,
+                                            bool packed, int g) {
+  constexpr int TPS = fft_tps(L);
+  constexpr float RH = 0.70710678118654752f;
+  const int N1 = a.n1;
+  const float2 fa0 = __ldg(a.fa + k1), fa1 = __ldg(a.fa + k1 + 1);
+  // 1/2 of the split folded into the a-twiddle (not for the packed item)
+  const float2 avr = make_float2(packed ? 1.f : 0.5f * fa0.x, 0.5f * fa1.x);
+  const float2 avi = make_float2(packed ? 0.f : 0.5f * fa0.y, 0.5f * fa1.y);
+  const bool rev = a.vkind == 1;  // DST-II: output (k1, k2) goes to (N1-1-k1, N2-1-k2)
+  const int kma = row_mirror(k1, N1), kmb = row_mirror(k1 + 1, N1);
+  float* ya0 = y + (long long)(rev ? N1 - 1 - k1 : k1) * L;
+  float* ya1 = y + (long long)(rev ? N1 - 1 - kma : kma) * L;
+  float* yb0 = y + (long long)(rev ? N1 - 1 - (k1 + 1) : k1 + 1) * L;
+  float* yb1 = y + (long long)(rev ? N1 - 1 - kmb : kmb) * L;
+  auto column = [&](int c) {
+    const soa::C2 P = soa::unpack(s[soa::pidx4(c)]);
+    const soa::C2 M = soa::unpack(s[soa::pidx4((L - c) & (L - 1))]);
+    const soa::C2 aP = soa::mulw(P, avr, avi), aM = soa::mulw(M, avr, avi);
+    const soa::C2 u{soa::add2(aP.re, aM.re), soa::sub2(aP.im, aM.im)};
+    soa::C2 w{soa::sub2(aP.re, aM.re), soa::add2(aP.im, aM.im)};
+    if (packed) {
+      w.re.x = RH * (M.re.x - P.re.x);
+      w.im.x = -RH * (P.im.x + M.im.x);
     }
-    pipe::mbar_arrive_expect_tx(bar, bytes);
-    for (int i = 0; i < R::NI; ++i) {
-      const float *ra, *rb;
-      row_sources<L, INV>(a, b, k0 + i, &ra, &rb);
-      if (ra) pipe::bulk_load(stage + i * 2 * L, ra, 4u * L, bar);
-      pipe::bulk_load(stage + i * 2 * L + L, rb, 4u * L, bar);
+    const float2 bt = __ldg(a.fb + c);
+    const soa::C2 sv = soa::mulw(u, soa::bc(bt.x), soa::bc(bt.y));
+    const soa::C2 tv = soa::mulw(w, soa::bc(bt.x), soa::bc(bt.y));
+    const int c0 = rev ? L - 1 - c : c, c1 = rev ? c - 1 : L - c;  // stored columns of c and L-c
+    ya0[c0] = sv.re.x;
+    yb0[c0] = sv.re.y;
+    ya1[c0] = -tv.im.x;
+    yb1[c0] = -tv.im.y;
+    if (c != 0 && c != L / 2) {
+      ya0[c1] = -sv.im.x;
+      yb0[c1] = -sv.im.y;
+      ya1[c1] = -tv.re.x;
+      yb1[c1] = -tv.re.y;
     }
-    ++issued;
   };
+#pragma unroll 2
+  for (int r = 0; r < L / 2 / TPS; ++r) column(g + TPS * r);
+  if (g == 0) column(L / 2);
+}
 
-  if (threadIdx.x == 0) {
-    pipe::mbar_init(bar, 1);
-    pipe::fence_mbar_init();
-  }
+template <int L>
+__global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB) k_fs2_rows_fwd_x2(Dct2dArgs a) {
+  using R = RowX2Geom<L>;
+  extern __shared__ float4 sxf[];
+  const int pi = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
+  float4* s = sxf + pi * R::LP;
+  const int k1 = 2 * (blockIdx.x * R::NP + pi);  // items k1 (lane a), k1 + 1 (lane b)
+  const float2* Zw = a.work + (long long)blockIdx.z * a.work_bstride;
+  const float2 *za, *ma, *zb, *mb;
+  fwd_rows_of<L>(a, Zw, k1, &za, &ma);
+  fwd_rows_of<L>(a, Zw, k1 + 1, &zb, &mb);
+  soa::C2 v[16];
+  const bool packed = (k1 == 0);
+  const int t = mirror_lane_butterfly<R::TPS>(g);
+  fwd_split_x2<L>(za, ma, zb, mb, t, packed, v);
+  soa::first_stage<L, false>(v, s, t);
   __syncthreads();
-  if (threadIdx.x == 0 && nk > 0) issue(0);
-  int done = 0;
-  for (int k = 0; k < nk; ++k) {
-    const bool ok = pipe::mbar_wait(bar, k & 1);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicExch(a.err, 1);
-      break;
-    }
-    done = k + 1;
-    const int u = blockIdx.x + k * gridDim.x;
-    const int b = u / upb, k1 = (u % upb) * R::NI + li;
-    const float* st = stage + li * 2 * L;
-    float2* s = fbuf + li * R::LP;
-    const float *ra, *rb;
-    row_sources<L, INV>(a, b, k1, &ra, &rb);
-    // row_item reads st, then synchronises before its first stage: the next
-    // group's copy may start after that barrier, so it is issued inside the
-    // item between the two (see below).
-    const bool packed = (k1 == 0);
-    const int kmir = row_mirror(k1, a.n1);
-    float2 v[16];
-    if constexpr (!INV)
-      fwd_split<L, R::TPS>(reinterpret_cast<const float2*>(st), packed, g, v);
-    else
-      inv_pre<L, R::TPS>(st, a, k1, packed, ra == nullptr, g, v);
-    __syncthreads();  // staging consumed by every thread
-    if (threadIdx.x == 0 && k + 1 < nk) {
-      pipe::fence_proxy_async();
-      issue(k + 1);
-    }
-    first_stage_regs<L, INV>(v, s, g);
-    __syncthreads();
-    fft_stages<L, 16, INV>(s, g, a.tw2);
-    if constexpr (!INV) {
-      fwd_post<L, R::TPS>(s, a, a.out + (long long)b * a.out_bstride, k1, kmir, packed, g);
+  soa::stages<L, 16, false>(s, g, a.tw2x);
+  fwd_post_x2<L>(s, a, a.out + (long long)blockIdx.z * a.out_bstride, k1, packed, g);
+}
+
+// Inverse four-read preprocess (Eq. 2d_idct_pre, conjugated twiddle, 1/(N1 N2)
+// in the a-table) of one item at the thread's points k2 = g + TPS j, as
+// (x, ia) pairs: x = (c1 - c2, -(c3 + c4)) b_k2 for a normal item, where
+// c1 = C(k1,k2), c3 = C(kmir,k2), c4 = C(k1,N2-k2), c2 = C(kmir,N2-k2) (zero
+// past the edge).  The kind's maps are folded into the reads: DST-II reads rows
+// N1-1-k and columns reversed; IDCT_IDXST swaps the reads at k2 and N2-k2
+// (column 0 zero); IDXST_IDCT swaps the item's two rows (row 0 zero).
+struct InvRows {
+  const float* ra;  // row of c1 / c4 (null: zero row)
+  const float* rb;  // row of c3 / c2
+};
+
+__device__ __forceinline__ InvRows inv_rows_of(const Dct2dArgs& a, const float* C, int k, int L) {
+  const int N1 = a.n1;
+  const int kmir = row_mirror(k, N1);
+  int r0 = k, r1 = kmir;
+  if (a.vkind == 1) {
+    r0 = N1 - 1 - k;
+    r1 = N1 - 1 - kmir;
+  }
+  InvRows r{C + (long long)r0 * L, C + (long long)r1 * L};
+  if (a.vkind == 3) {
+    if (k) {
+      const float* t = r.ra;
+      r.ra = r.rb;
+      r.rb = t;
     } else {
-      float2* Zw = a.work + (long long)b * a.work_bstride;
-      inv_pair<L, R::TPS>(s, Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2),
-                          Zw + (long long)fs2_prow(kmir, a.fsA, a.fsB) * (L / 2), packed, g);
+      r.ra = nullptr;
     }
-    __syncthreads();  // FFT buffer consumed before the next first stage
   }
-  // A copy issued but not waited for (only after a failed wait) must land
-  // before the CTA's shared memory is released.
-  if (threadIdx.x == 0 && issued > done) {
-    if (!pipe::mbar_wait(bar, done & 1)) atomicExch(a.err, 1);
+  return r;
+}
+
+// The four reads c1, c3, c4, c2 of point k2 of one item.
+template <int L, bool MAPPED>
+__device__ __forceinline__ float4 inv_reads(const InvRows& r, int k2, bool rev, bool swapc) {
+  const int km = (L - k2) & (L - 1);
+  float c1, c3, c4, c2;
+  if constexpr (!MAPPED) {
+    c1 = r.ra ? r.ra[k2] : 0.f;
+    c3 = r.rb[k2];
+    c4 = (k2 && r.ra) ? r.ra[km] : 0.f;
+    c2 = k2 ? r.rb[km] : 0.f;
+  } else {
+    const int ka = swapc ? km : k2, kb = swapc ? k2 : km;
+    const int pa = rev ? L - 1 - ka : ka, pb = rev ? L - 1 - kb : kb;
+    const bool z0 = swapc && !k2;
+    c1 = (!r.ra || z0) ? 0.f : r.ra[pa];
+    c3 = z0 ? 0.f : r.rb[pa];
+    c4 = (k2 && r.ra) ? r.ra[pb] : 0.f;
+    c2 = k2 ? r.rb[pb] : 0.f;
   }
+  return make_float4(c1, c3, c4, c2);
+}
+
+template <int L, bool MAPPED, bool PACKED>
+__device__ __forceinline__ void inv_pre_x2(const Dct2dArgs& a, const InvRows& A, const InvRows& B, int k1, int g,
+                                           soa::C2* v) {
+  constexpr int TPS = fft_tps(L);
+  const bool rev = MAPPED && a.vkind == 1, swapc = MAPPED && a.vkind == 2;
+  const float2 iaA = __ldg(a.ia + k1), iaB = __ldg(a.ia + k1 + 1);
+  const float2 ih = __ldg(a.ia + a.n1 / 2);
+  const float2 iar = make_float2(iaA.x, iaB.x), iai = make_float2(iaA.y, iaB.y);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int k2 = g + TPS * j;
+    const float4 ca = inv_reads<L, MAPPED>(A, k2, rev, swapc);
+    const float4 cb = inv_reads<L, MAPPED>(B, k2, rev, swapc);
+    const float2 bk = __ldg(a.ib + k2);
+    // x = (c1 - c2, -(c3 + c4)), v = x b ia
+    const soa::C2 x{make_float2(ca.x - ca.w, cb.x - cb.w), make_float2(-(ca.y + ca.z), -(cb.y + cb.z))};
+    v[j] = soa::mulw(soa::mulw(x, soa::bc(bk.x), soa::bc(bk.y)), iar, iai);
+    if constexpr (PACKED) {  // lane a: rows 0 and N1/2 packed as re / im of one sequence
+      const float2 v0 = cmul(cmul(make_float2(ca.x, -ca.z), bk), iaA);
+      const float2 vh = cmul(cmul(make_float2(ca.y - ca.w, -(ca.y + ca.w)), bk), ih);
+      v[j].re.x = v0.x - vh.y;
+      v[j].im.x = v0.y + vh.x;
+    }
+  }
+}
+
+// Inverse pairing of both items: row IFFT u in s -> workspace rows k1 and its
+// mirror: Z(k1, p) = u(p) + i u(L-1-p), Z(kmir, p) = conj(u(p)) + i conj(u(L-1-p)),
+// one column p per thread and iteration; packed lane a: the real and imaginary
+// parts go to rows 0 and N1/2.
+template <int L>
+__device__ __forceinline__ void inv_pair_x2(const float4* __restrict__ s, const Dct2dArgs& a, float2* Zw, int k1,
+                                            bool packed, int g) {
+  constexpr int TPS = fft_tps(L);
+  float2* za = Zw + (long long)fs2_prow(k1, a.fsA, a.fsB) * (L / 2);
+  float2* ma = Zw + (long long)fs2_prow(row_mirror(k1, a.n1), a.fsA, a.fsB) * (L / 2);
+  float2* zb = Zw + (long long)fs2_prow(k1 + 1, a.fsA, a.fsB) * (L / 2);
+  float2* mb = Zw + (long long)fs2_prow(row_mirror(k1 + 1, a.n1), a.fsA, a.fsB) * (L / 2);
+#pragma unroll 2
+  for (int r = 0; r < L / 2 / TPS; ++r) {
+    const int p = g + TPS * r;
+    const soa::C2 u = soa::unpack(s[soa::pidx4(p)]), w = soa::unpack(s[soa::pidx4(L - 1 - p)]);
+    zb[p] = make_float2(u.re.y - w.im.y, u.im.y + w.re.y);
+    mb[p] = make_float2(u.re.y + w.im.y, w.re.y - u.im.y);
+    za[p] = packed ? make_float2(u.re.x, w.re.x) : make_float2(u.re.x - w.im.x, u.im.x + w.re.x);
+    ma[p] = packed ? make_float2(u.im.x, w.im.x) : make_float2(u.re.x + w.im.x, w.re.x - u.im.x);
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB_INV) k_fs2_rows_inv_x2(Dct2dArgs a) {
+  using R = RowX2Geom<L>;
+  extern __shared__ float4 sxi[];
+  const int pi = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
+  float4* s = sxi + pi * R::LP;
+  const int k1 = 2 * (blockIdx.x * R::NP + pi);
+  const float* C = a.in + (long long)blockIdx.z * a.in_bstride;
+  const InvRows A = inv_rows_of(a, C, k1, L), B = inv_rows_of(a, C, k1 + 1, L);
+  const bool packed = (k1 == 0);
+  const bool mapped = a.vkind == 1 || a.vkind == 2;
+  soa::C2 v[16];
+  if (packed) {
+    if (mapped) inv_pre_x2<L, true, true>(a, A, B, k1, g, v);
+    else inv_pre_x2<L, false, true>(a, A, B, k1, g, v);
+  } else {
+    if (mapped) inv_pre_x2<L, true, false>(a, A, B, k1, g, v);
+    else inv_pre_x2<L, false, false>(a, A, B, k1, g, v);
+  }
+  soa::first_stage<L, true>(v, s, g);
+  __syncthreads();
+  soa::stages<L, 16, true>(s, g, a.tw2x);
+  inv_pair_x2<L>(s, a, a.work + (long long)blockIdx.z * a.work_bstride, k1, packed, g);
 }
 
 }  // namespace gbdct

@@ -59,8 +59,7 @@ struct Dct2dArgs {
   int fsA, fsB;       // four-step split N1 = A * B (four-step families)
   int vkind;          // kind whose index/sign maps the fs2 kernels fold into their
                       // loads and stores (0: DCT-II, no map; see dct2d_fs2_kernels.cuh)
-  int rows_mode;      // host side only (fs2): 0 staged row passes, 1 persistent prefetching row passes
-  int cols_mode;      // host side only (fs2): 0 vector column steps, 1 scalar (one column per thread)
+  const float4* tw2x; // stage twiddles for length N2 as (wr, wr, wi, wi) (fs2 two-item row passes)
   int nsm;            // host side only: multiprocessors of the device
 };
 

@@ -10,8 +10,6 @@
 
 #include "dct2d_kernels.cuh"
 #include "dct2d_pair_kernels.cuh"
-#include "dct2d_r64_kernels.cuh"
-#include "dct2d_fs_kernels.cuh"
 #include "dct2d_fs2_kernels.cuh"
 
 namespace gbdct {
@@ -45,36 +43,6 @@ cudaError_t run_fwd_cols2(int log2L, const Dct2dArgs& a, int npairs, int batch, 
 cudaError_t run_fwd_rows2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
 cudaError_t run_inv_rows2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
 cudaError_t run_inv_cols2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
-// Radix-64 passes for L in {4096, 8192}: `nitems` CTAs (two sequences each).
-cudaError_t run_fwd_cols_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
-cudaError_t run_fwd_rows_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
-cudaError_t run_inv_rows_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
-cudaError_t run_inv_cols_r64(int log2L, const Dct2dArgs& a, int nitems, int batch, cudaStream_t s, bool prepare);
-constexpr int kR64MinLog2 = 12;
-constexpr int kR64MaxLog2 = 13;
-
-template <int L>
-cudaError_t launch_r64(void (*kern)(Dct2dArgs), const Dct2dArgs& a, int nitems, int batch, cudaStream_t s,
-                       bool prepare) {
-  using G = R64Geom<L>;
-  if (prepare) {
-    return cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-  }
-  kern<<<dim3(nitems, batch), G::THREADS, G::SMEM, s>>>(a);
-  return cudaGetLastError();
-}
-
-// Four-step family: N1 in {1024, 2048, 4096}, N2 in {4096, 8192}.  One call
-// launches the whole forward (C1, C2, row pass) or inverse (row pass, C2', C1').
-cudaError_t run_fs(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, const float2* fstw, int batch,
-                   cudaStream_t s, bool prepare);
-constexpr int kFsMinLog2N1 = 10, kFsMaxLog2N1 = 12, kFsMinLog2N2 = 12, kFsMaxLog2N2 = 13;
-// Persistent pipelined four-step family: N1 in {1024, 2048, 4096}, N2 = 4096;
-// `nsm` persistent CTAs at most.
-cudaError_t run_fsp(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int batch, int nsm, cudaStream_t s,
-                    bool prepare);
-
 // Occupancy-first four-step family: N1 in {256, ..., 8192}, N2 in {256, ..., 16384}.
 cudaError_t run_fs2(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s,
                     bool prepare);
@@ -151,16 +119,6 @@ cudaError_t launch_pass(void (*kern)(Dct2dArgs), const Dct2dArgs& a, dim3 grid, 
       case 11: return launch_pair<2048>(KERN<2048>, a, np, nb, s, prep);                            \
       case 12: return launch_pair<4096>(KERN<4096>, a, np, nb, s, prep);                            \
       case 13: return launch_pair<8192>(KERN<8192>, a, np, nb, s, prep);                            \
-      default: return cudaErrorInvalidValue;                                                        \
-    }                                                                                               \
-  }
-
-// Defines run_<NAME>(log2L, ...) for the radix-64 kernels, L = 4096, 8192.
-#define GBDCT_DEFINE_R64_RUNNER(NAME, KERN)                                                         \
-  cudaError_t NAME(int log2L, const Dct2dArgs& a, int ni, int nb, cudaStream_t s, bool prep) {      \
-    switch (log2L) {                                                                                \
-      case 12: return launch_r64<4096>(KERN<4096>, a, ni, nb, s, prep);                             \
-      case 13: return launch_r64<8192>(KERN<8192>, a, ni, nb, s, prep);                             \
       default: return cudaErrorInvalidValue;                                                        \
     }                                                                                               \
   }

@@ -27,7 +27,7 @@ struct gbdct_plan_s {
   Dct2dArgs args;   // pointers and sizes shared by all passes
   int b_cols, b_rows;  // sequences per CTA of the column and row passes
   int family;          // kernel family (FAM_*)
-  float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS, FAM_FSP, FAM_FS2)
+  float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS2)
   int* err;            // device error word (bounded waits that gave up)
   int nsm;             // multiprocessors of the plan's device
   float* tmp;          // variant kinds: staging array (batch * N1 * N2 floats)
@@ -47,20 +47,26 @@ struct gbdct_plan_s {
 namespace {
 
 // Kernel families (all compute the same transform; chosen by size):
-//   FAM_FS2  four-step column steps + 16-point-per-thread row passes,
+//   FAM_FS2  four-step column steps + two-item row passes,
 //            N1 in {256..8192}, N2 in {256..16384}
-//   FAM_FSP  FAM_FS as persistent TMA-bulk-copy pipelines, N1 in {1024..4096}, N2 = 4096
-//   FAM_FS   four-step column FFTs + radix-64 rows, N1 in {1024..4096}, N2 in {4096, 8192}
-//   FAM_R64  radix-64 register FFTs, N1 and N2 in {4096, 8192}
 //   FAM_PAIR two interleaved sequences per thread, 16 <= N1, N2 <= 8192
 //   FAM_SEQ  one sequence per thread group, any supported size
-enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_R64 = 2, FAM_FS = 3, FAM_FSP = 4, FAM_FS2 = 5 };
+enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_FS2 = 5 };
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int64_t v) {
   int l = 0;
   while ((int64_t(1) << l) < v) ++l;
   return l;
+}
+
+// The stage twiddles of length L again as (wr, wr, wi, wi), for the two-lane
+// (packed FP32x2) FFT engine of fft_soa.cuh.
+__global__ void k_expand_twiddles(const float2* __restrict__ tw, float4* out, int total) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const float2 w = tw[idx];
+  out[idx] = make_float4(w.x, w.x, w.y, w.y);
 }
 
 // Stage twiddles of the Stockham FFT of length L (layout in fft_core.cuh):
@@ -344,8 +350,7 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
     if (dims[i] <= 0) return GBDCT_ERR_INVALID_ARG;
   if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
   if (dtype != GBDCT_F32) return GBDCT_ERR_UNSUPPORTED;
-  if (force && strcmp(force, "seq") && strcmp(force, "pair") && strcmp(force, "r64") && strcmp(force, "fs") &&
-      strcmp(force, "fsp") && strcmp(force, "fs2"))
+  if (force && strcmp(force, "seq") && strcmp(force, "pair") && strcmp(force, "fs2"))
     return GBDCT_ERR_INVALID_ARG;
   if (ndim == 3) return create_3d(out, dims, batch, kind, dtype, force);
   if (ndim != 2) return GBDCT_ERR_UNSUPPORTED;
@@ -372,29 +377,21 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   p->lg1 = ilog2(n1);
   p->lg2 = ilog2(n2);
 
-  const bool r64 = p->lg1 >= gbdct::kR64MinLog2 && p->lg1 <= gbdct::kR64MaxLog2 &&
-                   p->lg2 >= gbdct::kR64MinLog2 && p->lg2 <= gbdct::kR64MaxLog2;
   const bool pair = p->lg1 >= gbdct::kPairMinLog2 && p->lg1 <= gbdct::kPairMaxLog2 &&
                     p->lg2 >= gbdct::kPairMinLog2 && p->lg2 <= gbdct::kPairMaxLog2;
-  const bool fs = p->lg1 >= gbdct::kFsMinLog2N1 && p->lg1 <= gbdct::kFsMaxLog2N1 &&
-                  p->lg2 >= gbdct::kFsMinLog2N2 && p->lg2 <= gbdct::kFsMaxLog2N2;
-  const bool fsp = fs && p->lg2 == 12;
   const bool fs2 = p->lg1 >= gbdct::kFs2MinLog2N1 && p->lg1 <= gbdct::kFs2MaxLog2N1 &&
                    p->lg2 >= gbdct::kFs2MinLog2N2 && p->lg2 <= gbdct::kFs2MaxLog2N2;
   // Default: the occupancy-first four-step family where it applies, else the
   // two-sequence family, else one sequence per thread group (fastest measured
-  // at every shape they share); the other families are opt-in below.
+  // at every shape they share).
   p->family = fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
-  // GBDCT_KERNEL_FAMILY=seq|pair|r64|fs|fsp|fs2 forces a family when it supports the shape
+  // GBDCT_KERNEL_FAMILY=seq|pair|fs2 forces a family when it supports the shape
   // (used to test and compare every kernel family on the same inputs).
   if (const char* f = force ? force : getenv("GBDCT_KERNEL_FAMILY")) {
     const int before = p->family;
     int chosen = -1;
     if (!strcmp(f, "seq")) chosen = FAM_SEQ;
     else if (!strcmp(f, "pair") && pair) chosen = FAM_PAIR;
-    else if (!strcmp(f, "r64") && r64) chosen = FAM_R64;
-    else if (!strcmp(f, "fs") && fs) chosen = FAM_FS;
-    else if (!strcmp(f, "fsp") && fsp) chosen = FAM_FSP;
     else if (!strcmp(f, "fs2") && fs2) chosen = FAM_FS2;
     if (chosen < 0 && force) {
       delete p;
@@ -402,8 +399,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
     }
     p->family = chosen < 0 ? before : chosen;
   }
-  const bool four_step = p->family == FAM_FS || p->family == FAM_FSP || p->family == FAM_FS2;
-  p->pmax = (p->family == FAM_R64 || p->family == FAM_FS || p->family == FAM_FSP) ? gbdct::r64::PMAX : 16;
+  const bool four_step = p->family == FAM_FS2;
+  p->pmax = 16;
 
   // Table layout, each block padded to 2 float2 (16 B).
   const int tot1 = gbdct::tw_size_p(n1, p->pmax), tot2 = gbdct::tw_size_p(n2, p->pmax);
@@ -412,7 +409,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   const size_t ta = round_up(n1 / 2 + 1, 2);
   const size_t tb = round_up(n2, 2);
   const size_t tf = four_step ? round_up(n1, 2) : 0;
-  p->table_elems = t1 + t2 + 2 * ta + 2 * tb + tf + 2;  // + 16 bytes for the error word
+  const size_t tx = four_step ? 2 * t2 : 0;  // float4 copy of the N2 stage twiddles
+  p->table_elems = t1 + t2 + 2 * ta + 2 * tb + tf + tx + 2;  // + 16 bytes for the error word
   cudaError_t e = cudaMalloc(&p->tables, p->table_elems * sizeof(float2));
   if (e != cudaSuccess) {
     free_plan(p);
@@ -425,7 +423,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   float2* fb = ia + ta;
   float2* ib = fb + tb;
   p->fstw = four_step ? ib + tb : nullptr;
-  p->err = reinterpret_cast<int*>(ib + tb + tf);
+  float4* tw2x = four_step ? reinterpret_cast<float4*>(ib + tb + tf) : nullptr;
+  p->err = reinterpret_cast<int*>(ib + tb + tf + tx);
 
   p->work_bytes = (size_t)batch * (size_t)(n1 / 2) * (size_t)n2 * sizeof(float2);
   e = cudaMalloc(&p->work, p->work_bytes);
@@ -442,13 +441,9 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   const int nt = (n1 / 2 + 1 > n2) ? (n1 / 2 + 1) : n2;
   k_gen_dct_tables<<<(nt + 255) / 256, 256>>>(fa, fb, ia, ib, n1, n2);
   int fsA = 0, fsB = 0;
-  if (p->family == FAM_FS2) {
-    gbdct::fs2_split(p->lg1, &fsA, &fsB);
-  } else if (p->fstw) {
-    fsA = (n1 == 1024) ? 32 : 64;
-    fsB = n1 / fsA;
-  }
+  if (p->family == FAM_FS2) gbdct::fs2_split(p->lg1, &fsA, &fsB);
   if (p->fstw) k_gen_fs_twiddles<<<(n1 + 255) / 256, 256>>>(p->fstw, n1, fsA, fsB);
+  if (tw2x && tot2 > 0) k_expand_twiddles<<<(tot2 + 255) / 256, 256>>>(tw2, tw2x, tot2);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemset(p->err, 0, 16);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
@@ -467,6 +462,7 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   a.work = p->work;
   a.tw1 = tw1;
   a.tw2 = tw2;
+  a.tw2x = tw2x;
   a.fa = fa;
   a.fb = fb;
   a.ia = ia;
@@ -478,25 +474,12 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   a.fsB = fsB;
   a.vkind = p->family == FAM_FS2 ? kind : 0;
   a.nsm = p->nsm;
-  a.rows_mode = 0;  // GBDCT_FS2_ROWS=persistent|staged selects the fs2 row-pass variant
-  if (const char* rm = getenv("GBDCT_FS2_ROWS")) a.rows_mode = !strcmp(rm, "persistent") ? 1 : 0;
-  a.cols_mode = 0;  // GBDCT_FS2_COLS=scalar|vector selects the fs2 column-step form (N1 <= 4096)
-  if (const char* cm = getenv("GBDCT_FS2_COLS")) a.cols_mode = !strcmp(cm, "scalar") ? 1 : 0;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
 
   // Raise the dynamic shared-memory limit of the kernels once.
   if (p->family == FAM_FS2) {
     e = gbdct::run_fs2(p->lg1, p->lg2, false, a, 1, 0, true);
-  } else if (p->family == FAM_FSP) {
-    e = gbdct::run_fsp(p->lg1, p->lg2, false, a, 1, p->nsm, 0, true);
-  } else if (p->family == FAM_FS) {
-    e = gbdct::run_fs(p->lg1, p->lg2, false, a, p->fstw, 1, 0, true);
-  } else if (p->family == FAM_R64) {
-    e = gbdct::run_fwd_cols_r64(p->lg1, a, 1, 1, 0, true);
-    if (e == cudaSuccess) e = gbdct::run_inv_cols_r64(p->lg1, a, 1, 1, 0, true);
-    if (e == cudaSuccess) e = gbdct::run_fwd_rows_r64(p->lg2, a, 1, 1, 0, true);
-    if (e == cudaSuccess) e = gbdct::run_inv_rows_r64(p->lg2, a, 1, 1, 0, true);
   } else if (p->family == FAM_PAIR) {
     e = gbdct::run_fwd_cols2(p->lg1, a, 1, 1, 0, true);
     if (e == cudaSuccess) e = gbdct::run_inv_cols2(p->lg1, a, 1, 1, 0, true);
@@ -530,7 +513,7 @@ gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims,
 static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse,
                               int step = -1);
 static int core_launches(gbdct_plan_t p) {
-  return (p->family == FAM_FS || p->family == FAM_FSP || p->family == FAM_FS2) ? 3 : 2;
+  return p->family == FAM_FS2 ? 3 : 2;
 }
 
 static cudaError_t run_map(gbdct_plan_t p, const float* in, float* out, MapSpec m, cudaStream_t s) {
@@ -601,22 +584,6 @@ static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStr
   cudaError_t e = cudaSuccess;
   if (p->family == FAM_FS2) {
     return cuda_status(gbdct::run_fs2(p->lg1, p->lg2, inverse, a, batch, s, false));
-  }
-  if (p->family == FAM_FSP) {
-    return cuda_status(gbdct::run_fsp(p->lg1, p->lg2, inverse, a, batch, p->nsm, s, false));
-  }
-  if (p->family == FAM_FS) {
-    return cuda_status(gbdct::run_fs(p->lg1, p->lg2, inverse, a, p->fstw, batch, s, false));
-  }
-  if (p->family == FAM_R64) {
-    if (!inverse) {
-      if (s0) e = gbdct::run_fwd_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
-      if (e == cudaSuccess && s1) e = gbdct::run_fwd_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
-    } else {
-      if (s0) e = gbdct::run_inv_rows_r64(p->lg2, a, p->n1 / 4, batch, s, false);
-      if (e == cudaSuccess && s1) e = gbdct::run_inv_cols_r64(p->lg1, a, p->n2 / 4, batch, s, false);
-    }
-    return cuda_status(e);
   }
   if (p->family == FAM_PAIR) {
     if (!inverse) {
@@ -718,7 +685,7 @@ int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
 
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
   if (!plan) return "";
-  return plan->family == FAM_FS2 ? "fs2" : plan->family == FAM_FSP ? "fsp" : plan->family == FAM_FS ? "fs" : plan->family == FAM_R64 ? "r64" : plan->family == FAM_PAIR ? "pair" : "seq";
+  return plan->family == FAM_FS2 ? "fs2" : plan->family == FAM_PAIR ? "pair" : "seq";
 }
 
 gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan) {

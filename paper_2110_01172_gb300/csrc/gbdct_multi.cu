@@ -46,7 +46,7 @@ gbdct_status cuda_err(cudaError_t e) {
 // Autotuner
 // ---------------------------------------------------------------------------
 
-const char* const kFamilies[] = {"fs2", "pair", "seq", "r64", "fs", "fsp"};
+const char* const kFamilies[] = {"fs2", "pair", "seq"};
 
 std::mutex g_tune_mu;
 std::map<std::string, std::string>* g_tune = nullptr;  // key -> family

@@ -9,24 +9,10 @@ cudaError_t col_launch(const Dct2dArgs& a, int batch, cudaStream_t s, bool prepa
   using G = Fs2Geom<N1>;
   constexpr int S = (KIND == 0 || KIND == 3) ? G::B : G::A;
   using C = ColCfg<S>;
-  constexpr bool kScalar = S <= 64;  // the scalar (one column per thread) form covers S <= 64
-  constexpr size_t smem_s = (size_t)S * kCsCols * sizeof(float2);
   const int nslab = (KIND == 0 || KIND == 3) ? G::A : G::B;
   if (prepare) {
-    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_colv<N1, KIND>),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if constexpr (kScalar) {
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_col<N1, KIND>),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
-    }
-    return e;
-  }
-  if constexpr (kScalar) {
-    if (a.cols_mode == 1) {
-      k_fs2_col<N1, KIND><<<dim3(nslab, a.n2 / 2 / kCsCols, batch), kCsThreads, smem_s, s>>>(a);
-      return cudaGetLastError();
-    }
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_colv<N1, KIND>),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   }
   k_fs2_colv<N1, KIND><<<dim3(nslab, a.n2 / 2 / C::COLS, batch), C::THREADS, C::SMEM, s>>>(a);
   return cudaGetLastError();

@@ -10,44 +10,39 @@ namespace {
 
 template <int L>
 cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
-  using R = RowGeom<L>;
-  constexpr bool kPersistentFits = R::PSMEM <= 227 * 1024;
-  static int occ[2] = {0, 0};  // persistent CTAs per SM (forward, inverse), set at prepare
-  if (prepare) {
-    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows<L, false>),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows<L, true>),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
-    if constexpr (kPersistentFits) {
-      const void* pk[2] = {reinterpret_cast<const void*>(k_fs2p_rows<L, false>),
-                           reinterpret_cast<const void*>(k_fs2p_rows<L, true>)};
-      for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
-        e = cudaFuncSetAttribute(pk[d], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::PSMEM);
-        if (e == cudaSuccess)
-          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[d], pk[d], R::THREADS, R::PSMEM);
-      }
+  if constexpr (L <= 8192) {  // two items per thread group (packed two-lane arithmetic)
+    using R = RowX2Geom<L>;
+    if (prepare) {
+      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows_fwd_x2<L>),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows_inv_x2<L>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+      return e;
     }
-    return e;
-  }
-  if constexpr (kPersistentFits) {
-    if (a.rows_mode == 1 && occ[inverse] > 0) {
-      const int units = a.n1 / 2 / R::NI * batch;
-      const int want = occ[inverse] * a.nsm;
-      const int grid = units < want ? units : want;
-      if (inverse)
-        k_fs2p_rows<L, true><<<grid, R::THREADS, R::PSMEM, s>>>(a, batch);
-      else
-        k_fs2p_rows<L, false><<<grid, R::THREADS, R::PSMEM, s>>>(a, batch);
-      return cudaGetLastError();
+    const dim3 grid(a.n1 / 4 / R::NP, 1, batch);
+    if (inverse)
+      k_fs2_rows_inv_x2<L><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    else
+      k_fs2_rows_fwd_x2<L><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    using R = RowGeom<L>;
+    if (prepare) {
+      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows<L, false>),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows<L, true>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+      return e;
     }
+    const dim3 grid(a.n1 / 2 / R::NI, 1, batch);
+    if (inverse)
+      k_fs2_rows<L, true><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    else
+      k_fs2_rows<L, false><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    return cudaGetLastError();
   }
-  const dim3 grid(a.n1 / 2 / R::NI, 1, batch);
-  if (inverse)
-    k_fs2_rows<L, true><<<grid, R::THREADS, R::SMEM, s>>>(a);
-  else
-    k_fs2_rows<L, false><<<grid, R::THREADS, R::SMEM, s>>>(a);
-  return cudaGetLastError();
 }
 
 cudaError_t run_rows(int lg2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {

@@ -1,11 +1,16 @@
 """GPU parity of the 2D DCT-II / inverse against the FP64 oracle (needs a GB300).
 
 Acceptance (FP32): relative L2 error <= 1e-5 and max abs error <= 1e-4 max|X|
-against the oracle on the same float32 inputs.  Full comparisons run at sizes
-the oracle finishes in seconds (several FFT tiles, every power-of-two pair up
-to 128, rectangular up to 2048); the benchmark's 4096^2 and the largest sizes
-are checked on sampled entries computed one by one, plus the round trip.
+against the oracle on the same float32 inputs.  Every element is compared with
+the full oracle up to 8192^2 (the benchmark's 4096^2 included, with the launch
+configuration the benchmark times); only shapes with a side of 16384, whose
+dense oracle matrices alone take gigabytes, are checked on sampled entries
+computed one by one, plus the round trip.  The inverse is checked on a fixed
+float32 spectrum (the oracle forward of a seeded input, rounded), so a forward
+defect cannot be hidden by a mirrored inverse defect.
 """
+
+import functools
 
 import numpy as np
 import pytest
@@ -112,9 +117,37 @@ def _sample_indices(n1, n2, count, seed):
     return np.array(k1), np.array(k2)
 
 
-@pytest.mark.parametrize("shape", [(4096, 4096), (8192, 8192), (2048, 4096), (1024, 8192),
-                                   (16384, 1024), (2, 16384)])
-def test_large_sizes_sampled_entries_and_round_trip(shape):
+@functools.lru_cache(maxsize=4)
+def _oracle_pair(shape, seed):
+    """Seeded input x, its oracle forward X, a float32 spectrum Y (the oracle
+    forward rounded) and the oracle inverse of Y; cached per shape and seed."""
+    x = inputs.uniform(shape, seed=seed)
+    X = oracle.dct2_2d(x)
+    Y = X.astype(np.float32)
+    return x, X, Y, oracle.idct2_2d(Y)
+
+
+def _check_full(plan, shape, seed):
+    x, X, Y, y_ref = _oracle_pair(shape, seed)
+    Xg = plan.forward(torch.from_numpy(x).cuda())
+    yg = plan.inverse(torch.from_numpy(Y).cuda())
+    torch.cuda.synchronize()
+    check(Xg.cpu().numpy(), X)
+    check(yg.cpu().numpy(), y_ref)
+
+
+@pytest.mark.parametrize("shape", [(4096, 4096), (8192, 8192), (2048, 4096), (1024, 8192), (8192, 2048),
+                                   (4096, 8192), (4096, 1024)])
+def test_large_sizes_full_oracle(shape):
+    """Element-by-element forward and inverse against the full oracle at the
+    benchmark's 4096^2 and the other large 2D configurations."""
+    plan = _plan(shape)
+    _check_full(plan, shape, seed=0)
+    plan.close()
+
+
+@pytest.mark.parametrize("shape", [(16384, 1024), (2, 16384), (256, 16384)])
+def test_largest_sides_sampled_entries_and_round_trip(shape):
     n1, n2 = shape
     x = inputs.uniform(shape, seed=0)
     X, y = run_forward_inverse(x)
@@ -146,46 +179,28 @@ def test_bad_pointers_are_rejected():
 FAMILY_SUPPORT = {
     "seq": lambda s: True,
     "pair": lambda s: all(16 <= n <= 8192 for n in s),
-    "r64": lambda s: all(n in (4096, 8192) for n in s),
-    "fs": lambda s: s[0] in (1024, 2048, 4096) and s[1] in (4096, 8192),
-    "fsp": lambda s: s[0] in (1024, 2048, 4096) and s[1] == 4096,
     "fs2": lambda s: 256 <= s[0] <= 8192 and 256 <= s[1] <= 16384,
 }
 
 
-@pytest.mark.parametrize("family", ["seq", "pair", "r64", "fs", "fsp", "fs2"])
+@pytest.mark.parametrize("family", ["seq", "pair", "fs2"])
 @pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192), (1024, 4096),
                                    (8192, 2048)])
 def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
-    """Each kernel family, forced through GBDCT_KERNEL_FAMILY, on the same inputs."""
+    """Each kernel family, forced through GBDCT_KERNEL_FAMILY, element by
+    element against the full oracle on the same inputs."""
     if not FAMILY_SUPPORT[family](shape):
         pytest.skip(f"{family} does not support {shape}")
     monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
-    from paper_2110_01172_gb300 import Plan
+    from paper_2110_01172_gb300 import Plan, binding
     plan = Plan(shape, "dct2")
     assert plan.family == family
-    n1, n2 = shape
-    x = inputs.uniform(shape, seed=21)
-    xd = torch.from_numpy(x).cuda()
-    X = plan.forward(xd)
-    y = plan.inverse(X)
-    torch.cuda.synchronize()
-    Xh, yh = X.cpu().numpy(), y.cpu().numpy()
-    k1, k2 = _sample_indices(n1, n2, 40, seed=n1 * 7 + n2)
-    ref = oracle.dct2_2d_entries(x, k1, k2)
-    got = Xh[k1, k2].astype(np.float64)
-    assert np.abs(got - ref).max() <= MAX_ABS * np.abs(Xh).max()
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= REL_L2
-    j1, j2 = _sample_indices(n1, n2, 16, seed=n1 + 3 * n2)
-    ref_inv = oracle.idct2_2d_entries(Xh, j1, j2)
-    assert np.abs(yh[j1, j2] - ref_inv).max() <= MAX_ABS * np.abs(yh).max()
-    check(yh, x.astype(np.float64))
-    from paper_2110_01172_gb300 import binding
+    _check_full(plan, shape, seed=21)
     assert plan.check_device_error() == binding.OK
     plan.close()
 
 
-@pytest.mark.parametrize("family", ["fsp", "fs2"])
+@pytest.mark.parametrize("family", ["fs2"])
 def test_batched_four_step_families(family, monkeypatch):
     monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
     from paper_2110_01172_gb300 import Plan, binding
@@ -223,7 +238,7 @@ def test_small_families_full_oracle(family, shape, monkeypatch):
     check(y.cpu().numpy(), oracle.idct2_2d(X.cpu().numpy()))
 
 
-@pytest.mark.parametrize("family", ["pair", "fs", "fsp", "seq", "fs2"])
+@pytest.mark.parametrize("family", ["pair", "seq", "fs2"])
 def test_single_steps_compose_to_the_full_transform(family, monkeypatch):
     """gbdct_exec_step run for every launch in order equals the full call."""
     shape = (1024, 4096)
