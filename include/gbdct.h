@@ -97,8 +97,10 @@ const char* gbdct_version(void);
  *         65535, else GBDCT_ERR_UNSUPPORTED.  ndim 1 gives UNSUPPORTED.
  *   dims  ndim sizes; each must be a power of two between 2 and 16384, else
  *         GBDCT_ERR_UNSUPPORTED (dims <= 0 give GBDCT_ERR_INVALID_ARG).
- *   kind  a gbdct_kind; dtype must be GBDCT_F32.  Kinds other than
- *         GBDCT_DCT2 run the DCT-II kernels between two index/sign map kernels
+ *   kind  a gbdct_kind; dtype must be GBDCT_F32.  In the four-step family
+ *         (fs2) the index/sign maps of the other kinds are folded into the
+ *         first loads and last stores of the DCT-II kernels; the other
+ *         families run the DCT-II kernels between two index/sign map kernels
  *         and own an extra staging array of batch*N1*N2 floats.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises the device.
  */
@@ -144,7 +146,10 @@ gbdct_status gbdct_exec_step(gbdct_plan_t plan, int inverse, int step, const voi
 /* Short description of launch `step` (static storage; "" when out of range). */
 const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step);
 
-/* Bytes of device workspace owned by the plan (0 for a NULL plan). */
+/* Bytes of device workspace owned by the plan: the intermediate array, the
+ * staging array of mapped kinds (see gbdct_plan_create) and the DFT-GEMM
+ * operands of the split-BF16 mode (0 for a NULL plan).  Twiddle tables are not
+ * counted. */
 size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan);
 
 /* Number of kernel launches one exec call issues (0 for a NULL plan). */
@@ -265,7 +270,10 @@ gbdct_status gbdct_multi_destroy(gbdct_multi_t m);
  * with wu = pi u / N1, wv = pi v / N2 and the (0,0) term set to zero (the paper
  * only says "scaled a1, a2"; these are the eigenfrequencies of the cosine
  * basis in grid units).  The solver owns three plans (DCT2, IDXST_IDCT,
- * IDCT_IDXST) and the w tables (FP64-generated, stored FP32).
+ * IDCT_IDXST), the wu / wv tables and an N1 x N2 table of the eigenvalue
+ * denominators 1 / (wu^2 + wv^2), all evaluated in FP64 at creation and
+ * rounded once to FP32.  Calls switch to the solver's device for their
+ * duration.
  */
 typedef struct gbdct_poisson_s* gbdct_poisson_t;
 

@@ -39,10 +39,16 @@ __global__ void k_tw(float2* w, int N, int n) {
 }
 
 // ---------------------------------------------------------------- B1 kernels
+// Reorder (Eq. 2d_dct_pre): thread m of row r reads the adjacent pair
+// x[sigma1(r)][2m, 2m+1] as one float2 and stores v[r][m] = x[.][2m] and
+// v[r][N2-1-m] = x[.][2m+1] (both runs coalesced across the warp).
 __global__ void k_b1_pre(const float* __restrict__ x, float* __restrict__ v, int n1, int n2) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-  if (c >= n2) return;
-  v[(long long)r * n2 + c] = x[(long long)sigma(r, n1) * n2 + sigma(c, n2)];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (m >= n2 / 2) return;
+  const float2 p = reinterpret_cast<const float2*>(x + (long long)sigma(r, n1) * n2)[m];
+  float* vr = v + (long long)r * n2;
+  vr[m] = p.x;
+  vr[n2 - 1 - m] = p.y;
 }
 
 __global__ void k_b1_post(const float2* __restrict__ V, float* __restrict__ X, const float2* __restrict__ a,
@@ -77,10 +83,13 @@ __global__ void k_b1_ipre(const float* __restrict__ C, float2* __restrict__ V, c
   V[(long long)k1 * (n2 / 2 + 1) + k2] = make_float2(sc * z.x, sc * z.y);
 }
 
+// Inverse reorder (Eq. 2d_idct_post), the mirror of k_b1_pre: one float2 store
+// of x[sigma1(r)][2m, 2m+1] = (v[r][m], v[r][N2-1-m]) per thread.
 __global__ void k_b1_ipost(const float* __restrict__ v, float* __restrict__ x, int n1, int n2) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-  if (c >= n2) return;
-  x[(long long)sigma(r, n1) * n2 + sigma(c, n2)] = v[(long long)r * n2 + c];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (m >= n2 / 2) return;
+  const float* vr = v + (long long)r * n2;
+  reinterpret_cast<float2*>(x + (long long)sigma(r, n1) * n2)[m] = make_float2(vr[m], vr[n2 - 1 - m]);
 }
 
 // ---------------------------------------------------------------- B2 kernels
@@ -177,7 +186,7 @@ int gbdct_b1_create(gbdct_b1_s** out, int n1, int n2) {
 int gbdct_b1_forward(gbdct_b1_s* p, const float* x, float* X, void* stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int n1 = p->n1, n2 = p->n2;
-  k_b1_pre<<<dim3((n2 + 255) / 256, n1), 256, 0, s>>>(x, p->v, n1, n2);
+  k_b1_pre<<<dim3((n2 / 2 + 255) / 256, n1), 256, 0, s>>>(x, p->v, n1, n2);
   int st = cufftSetStream(p->r2c, s);
   if (!st) st = cufftExecR2C(p->r2c, p->v, reinterpret_cast<cufftComplex*>(p->V));
   k_b1_post<<<dim3((n2 / 2 + 1 + 255) / 256, n1 / 2 + 1), 256, 0, s>>>(p->V, X, p->a, p->b, n1, n2);
@@ -190,8 +199,22 @@ int gbdct_b1_inverse(gbdct_b1_s* p, const float* C, float* x, void* stream) {
   k_b1_ipre<<<dim3((n2 / 2 + 1 + 255) / 256, n1), 256, 0, s>>>(C, p->V, p->a, p->b, n1, n2);
   int st = cufftSetStream(p->c2r, s);
   if (!st) st = cufftExecC2R(p->c2r, reinterpret_cast<cufftComplex*>(p->V), p->v);
-  k_b1_ipost<<<dim3((n2 + 255) / 256, n1), 256, 0, s>>>(p->v, x, n1, n2);
+  k_b1_ipost<<<dim3((n2 / 2 + 255) / 256, n1), 256, 0, s>>>(p->v, x, n1, n2);
   return st ? st : (int)cudaGetLastError();
+}
+
+// The library FFTs of B1 alone (the paper's "RFFT2D" / "IRFFT2D" columns of
+// Table V): cuFFT 2D R2C of the plan's real buffer and C2R back into it.
+int gbdct_b1_r2c_only(gbdct_b1_s* p, void* stream) {
+  int st = cufftSetStream(p->r2c, reinterpret_cast<cudaStream_t>(stream));
+  if (!st) st = cufftExecR2C(p->r2c, p->v, reinterpret_cast<cufftComplex*>(p->V));
+  return st;
+}
+
+int gbdct_b1_c2r_only(gbdct_b1_s* p, void* stream) {
+  int st = cufftSetStream(p->c2r, reinterpret_cast<cudaStream_t>(stream));
+  if (!st) st = cufftExecC2R(p->c2r, reinterpret_cast<cufftComplex*>(p->V), p->v);
+  return st;
 }
 
 int gbdct_b1_destroy(gbdct_b1_s* p) {

@@ -659,8 +659,10 @@ struct RowX2Geom {
   static constexpr int THREADS = NP * TPS;
   static constexpr int LP = L + L / 16;                           // padded float4 per item pair
   static constexpr size_t SMEM = (size_t)NP * LP * sizeof(float4);
-  static constexpr int MINB = THREADS >= 512 ? 1 : 3;      // forward: CTAs per SM (80 registers)
-  static constexpr int MINB_INV = THREADS >= 512 ? 1 : 2;  // inverse (its preprocess needs more)
+  // CTAs per SM: two (up to 128 registers) measured faster than three at 80
+  // registers, where the compiler serialises the loads of the split
+  static constexpr int MINB = THREADS >= 512 ? 1 : 2;
+  static constexpr int MINB_INV = THREADS >= 512 ? 1 : 2;
 };
 
 // Column-spectrum rows of item k (row k1 and its mirror) in the workspace.

@@ -43,9 +43,11 @@ cudaError_t run_fwd_cols2(int log2L, const Dct2dArgs& a, int npairs, int batch, 
 cudaError_t run_fwd_rows2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
 cudaError_t run_inv_rows2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
 cudaError_t run_inv_cols2(int log2L, const Dct2dArgs& a, int npairs, int batch, cudaStream_t s, bool prepare);
-// Occupancy-first four-step family: N1 in {256, ..., 8192}, N2 in {256, ..., 16384}.
+// Four-step family: N1 in {256, ..., 8192}, N2 in {256, ..., 16384}.  One call
+// launches the whole forward (C1, C2, row pass) or inverse (row pass, C2', C1').
 cudaError_t run_fs2(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s,
                     bool prepare);
+cudaError_t run_fs2_col(int lg1, int kind, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare);
 constexpr int kFs2MinLog2N1 = 8, kFs2MaxLog2N1 = 13, kFs2MinLog2N2 = 8, kFs2MaxLog2N2 = 14;
 inline void fs2_split(int log2N1, int* A, int* B) {
   const int n1 = 1 << log2N1;

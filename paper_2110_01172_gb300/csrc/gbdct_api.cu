@@ -652,7 +652,9 @@ const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step) {
 }
 
 size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan) {
-  return plan ? plan->work_bytes + gbdct::gemm_workspace_bytes(plan->gemm) : 0;
+  if (!plan) return 0;
+  const size_t staging = plan->tmp ? (size_t)plan->batch * plan->n1 * plan->n2 * sizeof(float) : 0;
+  return plan->work_bytes + staging + gbdct::gemm_workspace_bytes(plan->gemm);
 }
 
 gbdct_status gbdct_plan_set_precision(gbdct_plan_t plan, int precision) {

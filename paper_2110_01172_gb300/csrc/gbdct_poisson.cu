@@ -6,6 +6,9 @@
 // "scaled electric potential a1, a2"; the scaling is the grid-unit
 // eigenfrequency reading of the cosine basis).  The transforms are the
 // library's own plans; one kernel applies the three spectral scalings.
+// The eigenvalue denominators 1 / (wu^2 + wv^2) are evaluated in FP64 once,
+// when the solver is created, and rounded once into an FP32 table that every
+// solve reads; wu and wv are FP64 values rounded once as well.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,41 +19,55 @@
 struct gbdct_poisson_s {
   int n1, n2, device;
   gbdct_plan_t fwd, fld0, fld1;  // DCT2 (forward and potential inverse), IDXST_IDCT, IDCT_IDXST
-  float* w;                           // wu[N1], wu^2[N1], wv[N2], wv^2[N2]
+  float* w;    // wu[N1], wv[N2]
+  float* inv;  // 1 / (wu^2 + wv^2) per (u, v), 0 at (0, 0): N1 x N2
 };
 
 namespace {
 
-// w tables in FP64, rounded once: wu = pi u / N1, wu2 = wu^2 (same for v).
+// Eigenfrequency tables in FP64, rounded once: wu = pi u / N1, wv = pi v / N2.
 __global__ void k_poisson_tables(float* w, int n1, int n2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n1) {
-    const double wu = 3.14159265358979323846 * (double)i / (double)n1;
-    w[i] = (float)wu;
-    w[n1 + i] = (float)(wu * wu);
-  }
-  if (i < n2) {
-    const double wv = 3.14159265358979323846 * (double)i / (double)n2;
-    w[2 * n1 + i] = (float)wv;
-    w[2 * n1 + n2 + i] = (float)(wv * wv);
-  }
+  if (i < n1) w[i] = (float)(3.14159265358979323846 * (double)i / (double)n1);
+  if (i < n2) w[n1 + i] = (float)(3.14159265358979323846 * (double)i / (double)n2);
+}
+
+// Eigenvalue denominators in FP64, rounded once: inv(u, v) = 1 / (wu^2 + wv^2),
+// inv(0, 0) = 0 (the DC term is zeroed).
+__global__ void k_poisson_denominators(float* inv, int n1, int n2) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int u = blockIdx.y;
+  if (v >= n2) return;
+  const double wu = 3.14159265358979323846 * (double)u / (double)n1;
+  const double wv = 3.14159265358979323846 * (double)v / (double)n2;
+  inv[(long long)u * n2 + v] = (u | v) ? (float)(1.0 / (wu * wu + wv * wv)) : 0.0f;
 }
 
 // In place on `a` (becomes a / den), and writes a wu / den, a wv / den.
 __global__ void k_poisson_scale(float* __restrict__ a, float* __restrict__ a1, float* __restrict__ a2,
-                                const float* __restrict__ w, int n1, int n2) {
+                                const float* __restrict__ w, const float* __restrict__ inv, int n1, int n2) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int u = blockIdx.y;
   if (v >= n2) return;
-  const float wu = __ldg(w + u), wu2 = __ldg(w + n1 + u);
-  const float wv = __ldg(w + 2 * n1 + v), wv2 = __ldg(w + 2 * n1 + n2 + v);
-  const float inv = (u | v) ? 1.0f / (wu2 + wv2) : 0.0f;
+  const float wu = __ldg(w + u), wv = __ldg(w + n1 + v);
   const long long idx = (long long)u * n2 + v;
-  const float val = a[idx] * inv;
+  const float val = a[idx] * __ldg(inv + idx);
   a[idx] = val;
   a1[idx] = val * wu;
   a2[idx] = val * wv;
 }
+
+// Makes the solver's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool switched = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) switched = (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
 
 void destroy(gbdct_poisson_s* p) {
   if (!p) return;
@@ -58,6 +75,7 @@ void destroy(gbdct_poisson_s* p) {
   gbdct_plan_destroy(p->fld0);
   gbdct_plan_destroy(p->fld1);
   if (p->w) cudaFree(p->w);
+  if (p->inv) cudaFree(p->inv);
   delete p;
 }
 
@@ -80,10 +98,12 @@ gbdct_status gbdct_poisson_create(gbdct_poisson_t* out, int64_t n1, int64_t n2) 
   p->n1 = (int)n1;
   p->n2 = (int)n2;
   cudaGetDevice(&p->device);
-  cudaError_t e = cudaMalloc(&p->w, 2 * (size_t)(n1 + n2) * sizeof(float));
+  cudaError_t e = cudaMalloc(&p->w, (size_t)(n1 + n2) * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->inv, (size_t)n1 * (size_t)n2 * sizeof(float));
   if (e == cudaSuccess) {
     const int m = (int)(n1 > n2 ? n1 : n2);
     k_poisson_tables<<<(m + 255) / 256, 256>>>(p->w, (int)n1, (int)n2);
+    k_poisson_denominators<<<dim3((unsigned)((n2 + 255) / 256), (unsigned)n1), 256>>>(p->inv, (int)n1, (int)n2);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -99,12 +119,13 @@ gbdct_status gbdct_poisson_solve(gbdct_poisson_t p, const void* rho, void* psi, 
                                  void* stream) {
   if (!p || !rho || !psi || !xi0 || !xi1) return GBDCT_ERR_INVALID_ARG;
   if (psi == xi0 || psi == xi1 || xi0 == xi1) return GBDCT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   gbdct_status st = gbdct_exec_forward(p->fwd, rho, psi, stream);
   if (st != GBDCT_OK) return st;
   const dim3 grid((p->n2 + 255) / 256, p->n1);
   k_poisson_scale<<<grid, 256, 0, s>>>(static_cast<float*>(psi), static_cast<float*>(xi0),
-                                       static_cast<float*>(xi1), p->w, p->n1, p->n2);
+                                       static_cast<float*>(xi1), p->w, p->inv, p->n1, p->n2);
   if (cudaGetLastError() != cudaSuccess) return GBDCT_ERR_CUDA;
   st = gbdct_exec_inverse(p->fwd, psi, psi, stream);
   if (st == GBDCT_OK) st = gbdct_exec_inverse(p->fld0, xi0, xi0, stream);
@@ -115,11 +136,12 @@ gbdct_status gbdct_poisson_solve(gbdct_poisson_t p, const void* rho, void* psi, 
 size_t gbdct_poisson_workspace_bytes(gbdct_poisson_t p) {
   if (!p) return 0;
   return gbdct_plan_workspace_bytes(p->fwd) + gbdct_plan_workspace_bytes(p->fld0) + gbdct_plan_workspace_bytes(p->fld1) +
-         2 * (size_t)p->n1 * p->n2 * sizeof(float) /* staging of the two IDXST plans */ +
-         2 * (size_t)(p->n1 + p->n2) * sizeof(float);
+         (size_t)p->n1 * p->n2 * sizeof(float) /* denominators */ + (size_t)(p->n1 + p->n2) * sizeof(float);
 }
 
 gbdct_status gbdct_poisson_destroy(gbdct_poisson_t p) {
+  if (!p) return GBDCT_OK;
+  DeviceGuard guard(p->device);
   destroy(p);
   return GBDCT_OK;
 }

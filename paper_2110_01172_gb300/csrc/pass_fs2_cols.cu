@@ -1,4 +1,4 @@
-// pass_fs2_cols.cu - column steps of the occupancy-first four-step family.
+// pass_fs2_cols.cu - column steps of the four-step family.
 #include "dct2d_launch.cuh"
 
 namespace gbdct {

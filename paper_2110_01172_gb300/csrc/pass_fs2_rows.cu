@@ -4,8 +4,6 @@
 
 namespace gbdct {
 
-cudaError_t run_fs2_col(int lg1, int kind, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare);
-
 namespace {
 
 template <int L>

@@ -18,8 +18,10 @@ def test_admission_controller_budget():
 
 
 def test_request_bytes_grows_with_area():
-    assert request_bytes((128, 128)) > 3.9 * request_bytes((64, 64))
-    assert request_bytes((2048, 2048)) > 100 * 2 ** 20
+    # 40 bytes per element (plans, staging, denominators, the four arrays) on
+    # top of a fixed margin for the graph
+    assert request_bytes((128, 128)) - request_bytes((64, 64)) >= 40 * (128 * 128 - 64 * 64)
+    assert request_bytes((2048, 2048)) > 160 * 2 ** 20
 
 
 def test_arrivals_and_shapes_are_seeded():
@@ -42,6 +44,19 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     for m, a in zip(mixed, alone):
         for x, y in zip(m.outputs, a.outputs):
             assert torch.equal(x, y)   # bitwise: the kernels and plan choice depend only on the shape
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [(64, 64), (128, 2048), (256, 256), (2048, 2048)])
+def test_admission_charge_covers_what_a_resident_solve_holds(shape):
+    """request_bytes (what admission reserves) is at least the measured device
+    bytes of a resident solve: solver workspaces and tables, the four arrays
+    and what the CUDA-graph capture allocates in its private pool."""
+    torch = pytest.importorskip("torch")
+    from paper_2110_01172_gb300.serving import _Resources
+    res = _Resources(shape, torch.device("cuda", 0), graph=True)
+    assert 0 < res.device_bytes <= request_bytes(shape)
+    res.close()
 
 
 @pytest.mark.gpu

@@ -51,7 +51,7 @@ class FakeRes:
         self.shape = shape
         self.closed = False
 
-    def launch(self, rho, stream):
+    def launch(self, rho, stream, ingress=None):
         FakeRes.order.append(rho)
 
 
@@ -67,6 +67,7 @@ def make_server(slots, budget):
     srv.graphs = False
     srv.block_horizon = 0.0
     srv.made = []
+    srv._ingress = lambda slot, numel: None
 
     def make(shape):
         r = FakeRes(shape)
@@ -82,6 +83,9 @@ class Payload:
     def __init__(self, shape, tag):
         self.shape = shape
         self.tag = tag
+
+    def numel(self):
+        return self.shape[0] * self.shape[1]
 
     def __repr__(self):
         return f"P{self.tag}"

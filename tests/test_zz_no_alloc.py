@@ -50,6 +50,26 @@ def test_noalloc_matches_plan_forward_on_two_calls_in_a_row():
 
 
 @pytest.mark.gpu
+def test_noalloc_one_sequence_kernels_and_in_place():
+    """Shapes with a side below 16 or equal to 16384 take the one-sequence
+    passes (a different grid and shared-memory size); in == out is allowed."""
+    from paper_2110_01172_gb300 import Plan
+    lib = binding.load()
+    for shape, seed in (((16384, 64), 3), ((8, 4096), 4), ((2, 2), 5), ((64, 16384), 6)):
+        x = torch.from_numpy(inputs.uniform(shape, seed=seed)).cuda()
+        out = torch.empty_like(x)
+        assert _noalloc_call(lib, x, out) == binding.OK
+        ref = Plan(shape, "dct2").forward(x)
+        torch.cuda.synchronize()
+        _compare(out, ref)
+    x = torch.from_numpy(inputs.uniform((512, 512), seed=7)).cuda()
+    ref = Plan((512, 512), "dct2").forward(x)
+    assert _noalloc_call(lib, x, x) == binding.OK    # in place
+    torch.cuda.synchronize()
+    _compare(x, ref)
+
+
+@pytest.mark.gpu
 def test_noalloc_rejects_sizes_beyond_its_limit():
     lib = binding.load()
     x = torch.zeros((2048, 1024), device="cuda")
