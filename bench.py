@@ -420,9 +420,9 @@ def run_configs(dev, peak):
     for kind in ("dst2", "idct_idxst", "idxst_idct"):
         out["kinds_2048"].append(one((2048, 2048), kind))
 
-    # split-BF16 DFT-GEMM precision mode (tensor cores) beside the FP32 path
+    # split-BF16 DFT-GEMM precision mode (hand-written tcgen05 kernels) beside the FP32 path
     out["split_bf16"] = []
-    for shape, batch in (((1024, 1024), 1), ((256, 256), 64)):
+    for shape, batch in (((1024, 1024), 1), ((256, 256), 64), ((2048, 2048), 1)):
         p32 = Plan(shape, batch=batch)
         pg = Plan(shape, batch=batch).set_precision("split_bf16")
         full = ((batch,) if batch > 1 else ()) + shape

@@ -165,12 +165,20 @@ int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
 
 /* Reports (and clears) a failure recorded on the device by the plan's
- * kernels: the pipelined kernels bound every wait on an asynchronous copy, and
- * a wait that gives up records it here instead of hanging the GPU (the
- * transform's output is then invalid).  Synchronises with the device.
- * Returns GBDCT_OK, GBDCT_ERR_TIMEOUT, GBDCT_ERR_INVALID_ARG (NULL plan) or
- * GBDCT_ERR_CUDA. */
+ * kernels: the pipelined tensor-core kernels of the split-BF16 mode bound every
+ * wait on an asynchronous copy or MMA, and a wait that gives up records it
+ * here instead of hanging the GPU (the kernel then waits for the work it has
+ * already issued and leaves its output tile unwritten, so the transform's
+ * output is invalid).  Synchronises with the device.  Returns GBDCT_OK,
+ * GBDCT_ERR_TIMEOUT, GBDCT_ERR_INVALID_ARG (NULL plan) or GBDCT_ERR_CUDA. */
 gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan);
+
+/* Bound of every device-side wait of the plan's pipelined kernels, in polls of
+ * the waited-on barrier (0, the default, is about half a second; a 3D plan
+ * passes it to its 2D slices).  A diagnostic: a tiny bound makes the waits
+ * give up, which is how the timeout path (gbdct_plan_check_device_error) is
+ * tested without a device fault.  Errors: INVALID_ARG (NULL plan). */
+gbdct_status gbdct_plan_set_wait_limit(gbdct_plan_t plan, uint32_t polls);
 
 /* Release the plan and its device memory.  NULL is accepted (no-op).  The
  * caller must make sure no stream still uses the plan. */
@@ -203,14 +211,15 @@ gbdct_status gbdct_plan_create_tuned(gbdct_plan_t* out, int ndim, const int64_t*
 /*
  * Precision mode of a plan.  GBDCT_PREC_SPLIT_BF16 evaluates the separable
  * definition as dense products, X = C1 x C2^T forward and x = D1 X D2^T
- * inverse (C the DCT-II matrix, D its exact inverse), on the tensor cores:
- * every operand is split into bf16 hi + lo parts and each product is
- * accumulated in FP32 as hi*hi + hi*lo + lo*hi.  Its error is that of the
- * split (about 1e-5 relative in L2, stated per result), not the FP32 path's.
- * Supported for 2D GBDCT_DCT2 plans with both sides <= 2048 (UNSUPPORTED
- * otherwise); the first switch allocates the matrices (FP64-generated, split
- * once) and 2 bf16 + 1 FP32 arrays of batch*N1*N2 and synchronises the device.
- * gbdct_exec_step is UNSUPPORTED in this mode.  GBDCT_PREC_FP32 switches back.
+ * inverse (C the DCT-II matrix, D its exact inverse), on the tensor cores by
+ * a hand-written tcgen05 kernel: every operand is split into bf16 hi + lo
+ * parts and each product is accumulated in FP32 (in tensor memory) as
+ * hi*hi + hi*lo + lo*hi.  Its error is that of the split (about 5e-6 relative
+ * in L2, stated per result), not the FP32 path's.  Supported for 2D GBDCT_DCT2
+ * plans with both sides between 128 and 2048 (UNSUPPORTED otherwise); the
+ * first switch allocates the matrices (FP64-generated, split once) and four
+ * bf16 arrays of batch*N1*N2 and synchronises the device.  gbdct_exec_step is
+ * UNSUPPORTED in this mode.  GBDCT_PREC_FP32 switches back.
  * Errors: INVALID_ARG (NULL plan, unknown mode), UNSUPPORTED, OOM, CUDA.
  */
 gbdct_status gbdct_plan_set_precision(gbdct_plan_t plan, int precision);

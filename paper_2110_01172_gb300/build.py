@@ -77,10 +77,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if log.strip():
                 print(f"== {os.path.basename(s)}\n{log}")
     tmp = library_path() + ".tmp"
-    # cuBLAS (the GEMMs of the split-BF16 precision mode) from the toolkit
-    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lcublas",
-           "-Xlinker", "-rpath", "-Xlinker", cuda_lib]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

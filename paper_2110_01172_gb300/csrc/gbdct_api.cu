@@ -42,6 +42,7 @@ struct gbdct_plan_s {
   int lg0;
   int precision;             // GBDCT_PREC_FP32 (FFT kernels) or GBDCT_PREC_SPLIT_BF16
   gbdct::GemmPath* gemm;     // split-BF16 DFT-GEMM state (precision mode only)
+  uint32_t wait_polls;       // bound of device-side waits (0: default), see gbdct_plan_set_wait_limit
 };
 
 namespace {
@@ -665,13 +666,15 @@ gbdct_status gbdct_plan_set_precision(gbdct_plan_t plan, int precision) {
   }
   if (precision != GBDCT_PREC_SPLIT_BF16) return GBDCT_ERR_INVALID_ARG;
   if (plan->ndim != 2 || plan->kind != GBDCT_DCT2) return GBDCT_ERR_UNSUPPORTED;
-  if (plan->n1 > gbdct::kGemmMaxSide || plan->n2 > gbdct::kGemmMaxSide || plan->batch > 65535)
+  if (plan->n1 > gbdct::kGemmMaxSide || plan->n2 > gbdct::kGemmMaxSide || plan->n1 < gbdct::kGemmMinSide ||
+      plan->n2 < gbdct::kGemmMinSide || plan->batch > 65535)
     return GBDCT_ERR_UNSUPPORTED;
   if (!plan->gemm) {
     DeviceGuard guard(plan->device);
     gbdct_status st = GBDCT_OK;
-    plan->gemm = gbdct::gemm_create(plan->n1, plan->n2, (int)plan->batch, &st);
+    plan->gemm = gbdct::gemm_create(plan->n1, plan->n2, (int)plan->batch, plan->err, &st);
     if (!plan->gemm) return st;
+    gbdct::gemm_set_wait_polls(plan->gemm, plan->wait_polls);
   }
   plan->precision = GBDCT_PREC_SPLIT_BF16;
   return GBDCT_OK;
@@ -679,7 +682,7 @@ gbdct_status gbdct_plan_set_precision(gbdct_plan_t plan, int precision) {
 
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (!plan) return 0;
-  if (plan->precision == GBDCT_PREC_SPLIT_BF16) return 8;  // 2 split kernels + 6 GEMMs (library launches may add more)
+  if (plan->precision == GBDCT_PREC_SPLIT_BF16) return 3;  // split kernel + two tensor-core products
   if (plan->ndim == 3) return gbdct_plan_launches_per_exec(plan->inner) + 1;
   const int core = core_launches(plan);
   return (plan->kind == GBDCT_DCT2 || plan->family == FAM_FS2) ? core : core + 2;
@@ -688,6 +691,14 @@ int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
   if (!plan) return "";
   return plan->family == FAM_FS2 ? "fs2" : plan->family == FAM_PAIR ? "pair" : "seq";
+}
+
+gbdct_status gbdct_plan_set_wait_limit(gbdct_plan_t plan, uint32_t polls) {
+  if (!plan) return GBDCT_ERR_INVALID_ARG;
+  if (plan->ndim == 3) return gbdct_plan_set_wait_limit(plan->inner, polls);
+  plan->wait_polls = polls;
+  gbdct::gemm_set_wait_polls(plan->gemm, polls);
+  return GBDCT_OK;
 }
 
 gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan) {
