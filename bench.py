@@ -417,6 +417,20 @@ def run_configs(dev, peak):
         out["2d"].append(one(shape))
     for shape in [(128, 128, 128), (256, 256, 256)]:
         out["3d"].append(one(shape))
+    # the autotuner's tile candidates: the four-step split N1 = A * (N1 / A)
+    out["fs2_splits"] = []
+    for shape in [(4096, 4096), (2048, 2048), (8192, 8192), (1024, 8192)]:
+        for a in (16, 32, 64, 128):
+            if not 16 <= shape[0] // a <= 128:
+                continue
+            plan = Plan(shape, family=f"fs2/{a}")
+            xs = [torch.rand(shape, device=dev) * 2 - 1 for _ in range(2)]
+            ys = [torch.empty_like(xs[0]) for _ in range(2)]
+            out["fs2_splits"].append({
+                "shape": list(shape), "A": a, "B": shape[0] // a,
+                "fwd_us": _event_loop_us(lambda i: plan.forward(xs[i % 2], ys[i % 2]), 20, stream),
+                "inv_us": _event_loop_us(lambda i: plan.inverse(xs[i % 2], ys[i % 2]), 20, stream)})
+            plan.close()
     for kind in ("dst2", "idct_idxst", "idxst_idct"):
         out["kinds_2048"].append(one((2048, 2048), kind))
 

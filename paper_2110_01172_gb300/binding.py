@@ -159,11 +159,14 @@ class Plan:
         dims = (ctypes.c_int64 * len(self.shape))(*self.shape)
         handle = ctypes.c_void_p()
         args = (ctypes.byref(handle), len(self.shape), dims, self.batch, KINDS[kind], F32)
+        self.choice = family   # the forced or tuned family / four-step split, e.g. "fs2/32"
         with torch.cuda.device(self.device):
             if family is not None:
                 _check(lib.gbdct_plan_create_family(*args, family.encode()), "gbdct_plan_create_family")
             elif tuned:
-                _check(lib.gbdct_plan_create_tuned(*args, None, 0), "gbdct_plan_create_tuned")
+                buf = ctypes.create_string_buffer(32)
+                _check(lib.gbdct_plan_create_tuned(*args, buf, 32), "gbdct_plan_create_tuned")
+                self.choice = buf.value.decode()
             else:
                 _check(lib.gbdct_plan_create_batched(*args), "gbdct_plan_create")
         self._h = handle
@@ -174,7 +177,7 @@ class Plan:
         return int(self._lib.gbdct_plan_workspace_bytes(self._h))
 
     def set_precision(self, precision: str):
-        """"fp32" (the FFT kernels) or "split_bf16" (tensor-core DFT-GEMMs, ~1e-5 error)."""
+        """"fp32" (the FFT kernels) or "split_bf16" (tcgen05 tensor-core DFT-GEMMs, ~5e-6 error)."""
         modes = {"fp32": 0, "split_bf16": 1}
         if precision not in modes:
             raise ValueError(f"unknown precision {precision!r}")

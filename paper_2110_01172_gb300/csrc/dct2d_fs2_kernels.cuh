@@ -50,10 +50,13 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
-template <int N1>
+// Four-step split N1 = A * B of the column FFT (a tile parameter: the slabs of
+// the column steps are A or B rows); both factors in {16, 32, 64, 128}.
+template <int N1, int A_>
 struct Fs2Geom {
-  static constexpr int A = (N1 >= 2048) ? 64 : (N1 >= 512 ? 32 : 16);
-  static constexpr int B = N1 / A;  // 128 for N1 = 8192 (vector column steps only)
+  static constexpr int A = A_;
+  static constexpr int B = N1 / A_;
+  static_assert(A >= 16 && A <= 128 && B >= 16 && B <= 128, "four-step factors out of range");
 };
 
 // Physical workspace row of column-spectrum row k1 (A, B powers of two).
@@ -281,11 +284,11 @@ __device__ __forceinline__ float4 vsign(float4 v, float sr, float sc) {
   return make_float4(sr * v.x, sc * v.y, sr * v.z, sc * v.w);
 }
 
-template <int N1, int KIND>
-__global__ void __launch_bounds__(ColCfg<(KIND == 0 || KIND == 3) ? Fs2Geom<N1>::B : Fs2Geom<N1>::A>::THREADS,
-                                  1024 / ColCfg<(KIND == 0 || KIND == 3) ? Fs2Geom<N1>::B : Fs2Geom<N1>::A>::THREADS)
+template <int N1, int A, int KIND>
+__global__ void __launch_bounds__(ColCfg<(KIND == 0 || KIND == 3) ? N1 / A : A>::THREADS,
+                                  1024 / ColCfg<(KIND == 0 || KIND == 3) ? N1 / A : A>::THREADS)
 k_fs2_colv(Dct2dArgs a) {
-  using G = Fs2Geom<N1>;
+  using G = Fs2Geom<N1, A>;
   constexpr bool INV = KIND >= 2;
   constexpr int S = (KIND == 0 || KIND == 3) ? G::B : G::A;
   using C = ColCfg<S>;
@@ -893,7 +896,9 @@ __device__ __forceinline__ void inv_pair_x2(const float4* __restrict__ s, const 
   }
 }
 
-template <int L>
+// MAPPED: the DST-II / IDCT_IDXST index maps folded into the reads (a separate
+// instantiation, so the plain DCT-II inverse carries no code for them).
+template <int L, bool MAPPED>
 __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB_INV) k_fs2_rows_inv_x2(Dct2dArgs a) {
   using R = RowX2Geom<L>;
   extern __shared__ float4 sxi[];
@@ -903,15 +908,11 @@ __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB_INV)
   const float* C = a.in + (long long)blockIdx.z * a.in_bstride;
   const InvRows A = inv_rows_of(a, C, k1, L), B = inv_rows_of(a, C, k1 + 1, L);
   const bool packed = (k1 == 0);
-  const bool mapped = a.vkind == 1 || a.vkind == 2;
   soa::C2 v[16];
-  if (packed) {
-    if (mapped) inv_pre_x2<L, true, true>(a, A, B, k1, g, v);
-    else inv_pre_x2<L, false, true>(a, A, B, k1, g, v);
-  } else {
-    if (mapped) inv_pre_x2<L, true, false>(a, A, B, k1, g, v);
-    else inv_pre_x2<L, false, false>(a, A, B, k1, g, v);
-  }
+  if (packed)
+    inv_pre_x2<L, MAPPED, true>(a, A, B, k1, g, v);
+  else
+    inv_pre_x2<L, MAPPED, false>(a, A, B, k1, g, v);
   soa::first_stage<L, true>(v, s, g);
   __syncthreads();
   soa::stages<L, 16, true>(s, g, a.tw2x);

@@ -49,9 +49,11 @@ cudaError_t run_fs2(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, in
                     bool prepare);
 cudaError_t run_fs2_col(int lg1, int kind, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare);
 constexpr int kFs2MinLog2N1 = 8, kFs2MaxLog2N1 = 13, kFs2MinLog2N2 = 8, kFs2MaxLog2N2 = 14;
+// Default four-step split N1 = A * B (the autotuner may choose another one,
+// gbdct_plan_create_tuned); A = 16 at N1 = 2048 measured faster than 32 or 64.
 inline void fs2_split(int log2N1, int* A, int* B) {
   const int n1 = 1 << log2N1;
-  *A = (n1 >= 2048) ? 64 : (n1 >= 512 ? 32 : 16);
+  *A = (n1 == 2048) ? 16 : (n1 >= 4096) ? 64 : (n1 >= 512 ? 32 : 16);
   *B = n1 / *A;
 }
 

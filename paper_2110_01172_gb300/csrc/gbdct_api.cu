@@ -351,8 +351,17 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
     if (dims[i] <= 0) return GBDCT_ERR_INVALID_ARG;
   if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
   if (dtype != GBDCT_F32) return GBDCT_ERR_UNSUPPORTED;
-  if (force && strcmp(force, "seq") && strcmp(force, "pair") && strcmp(force, "fs2"))
+  // a family name, or "fs2/<A>" for the four-step family with the split
+  // N1 = A * (N1 / A) of its column FFT (A and N1 / A in {16, 32, 64, 128})
+  const char* fname = force ? force : getenv("GBDCT_KERNEL_FAMILY");
+  int split_a = 0;
+  if (fname && strncmp(fname, "fs2/", 4) == 0) {
+    split_a = atoi(fname + 4);
+    if (split_a != 16 && split_a != 32 && split_a != 64 && split_a != 128) split_a = -1;
+  }
+  if (force && (split_a < 0 || (!split_a && strcmp(force, "seq") && strcmp(force, "pair") && strcmp(force, "fs2"))))
     return GBDCT_ERR_INVALID_ARG;
+  if (split_a < 0) split_a = 0;
   if (ndim == 3) return create_3d(out, dims, batch, kind, dtype, force);
   if (ndim != 2) return GBDCT_ERR_UNSUPPORTED;
   for (int i = 0; i < ndim; ++i) {
@@ -388,12 +397,13 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   p->family = fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
   // GBDCT_KERNEL_FAMILY=seq|pair|fs2 forces a family when it supports the shape
   // (used to test and compare every kernel family on the same inputs).
-  if (const char* f = force ? force : getenv("GBDCT_KERNEL_FAMILY")) {
+  if (const char* f = fname) {
     const int before = p->family;
     int chosen = -1;
     if (!strcmp(f, "seq")) chosen = FAM_SEQ;
     else if (!strcmp(f, "pair") && pair) chosen = FAM_PAIR;
     else if (!strcmp(f, "fs2") && fs2) chosen = FAM_FS2;
+    else if (split_a && fs2 && n1 / split_a >= 16 && n1 / split_a <= 128) chosen = FAM_FS2;
     if (chosen < 0 && force) {
       delete p;
       return GBDCT_ERR_UNSUPPORTED;
@@ -442,7 +452,13 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   const int nt = (n1 / 2 + 1 > n2) ? (n1 / 2 + 1) : n2;
   k_gen_dct_tables<<<(nt + 255) / 256, 256>>>(fa, fb, ia, ib, n1, n2);
   int fsA = 0, fsB = 0;
-  if (p->family == FAM_FS2) gbdct::fs2_split(p->lg1, &fsA, &fsB);
+  if (p->family == FAM_FS2) {
+    gbdct::fs2_split(p->lg1, &fsA, &fsB);
+    if (split_a && n1 / split_a >= 16 && n1 / split_a <= 128) {
+      fsA = split_a;
+      fsB = n1 / split_a;
+    }
+  }
   if (p->fstw) k_gen_fs_twiddles<<<(n1 + 255) / 256, 256>>>(p->fstw, n1, fsA, fsB);
   if (tw2x && tot2 > 0) k_expand_twiddles<<<(tot2 + 255) / 256, 256>>>(tw2, tw2x, tot2);
   e = cudaGetLastError();

@@ -46,7 +46,9 @@ gbdct_status cuda_err(cudaError_t e) {
 // Autotuner
 // ---------------------------------------------------------------------------
 
-const char* const kFamilies[] = {"fs2", "pair", "seq"};
+// candidates: the kernel families, and the four-step family with each split
+// N1 = A * (N1 / A) of its column FFT (tile shape of the column steps)
+const char* const kFamilies[] = {"fs2", "pair", "seq", "fs2/16", "fs2/32", "fs2/64", "fs2/128"};
 
 std::mutex g_tune_mu;
 std::map<std::string, std::string>* g_tune = nullptr;  // key -> family

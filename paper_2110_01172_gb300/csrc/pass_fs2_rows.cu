@@ -14,13 +14,18 @@ cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t
       cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows_fwd_x2<L>),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows_inv_x2<L>),
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows_inv_x2<L, false>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_fs2_rows_inv_x2<L, true>),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
       return e;
     }
     const dim3 grid(a.n1 / 4 / R::NP, 1, batch);
-    if (inverse)
-      k_fs2_rows_inv_x2<L><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    if (inverse && (a.vkind == 1 || a.vkind == 2))
+      k_fs2_rows_inv_x2<L, true><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    else if (inverse)
+      k_fs2_rows_inv_x2<L, false><<<grid, R::THREADS, R::SMEM, s>>>(a);
     else
       k_fs2_rows_fwd_x2<L><<<grid, R::THREADS, R::SMEM, s>>>(a);
     return cudaGetLastError();

@@ -15,8 +15,14 @@ SIZES = [256, 512, 1024, 2048, 4096, 8192]
 
 
 def split(n1):
-    a = 64 if n1 >= 2048 else (32 if n1 >= 512 else 16)
+    """The default four-step split N1 = A B."""
+    a = 16 if n1 == 2048 else (64 if n1 >= 4096 else (32 if n1 >= 512 else 16))
     return a, n1 // a
+
+
+# every split the column steps are built for (A and B in {16, 32, 64, 128});
+# the autotuner chooses among them
+SPLITS = [(n1, a) for n1 in SIZES for a in (16, 32, 64, 128) if 16 <= n1 // a <= 128]
 
 
 def reorder_src(n, length):
@@ -33,9 +39,9 @@ def prow(k1, a, b):
     return (k1 % b) * a + k1 // b
 
 
-@pytest.mark.parametrize("n1", SIZES)
-def test_column_steps_touch_every_row_once(n1):
-    a, b = split(n1)
+@pytest.mark.parametrize("n1,a", SPLITS)
+def test_column_steps_touch_every_row_once(n1, a):
+    b = n1 // a
     assert a * b == n1
     for kind in range(4):
         s = b if kind in (0, 3) else a          # DFT length of the step
@@ -73,11 +79,11 @@ def test_column_steps_touch_every_row_once(n1):
             assert sorted(twiddles) == list(range(n1))   # the W_N1 table has N1 entries, each used once
 
 
-@pytest.mark.parametrize("n1", SIZES)
-def test_four_step_layout_is_the_column_spectrum_order(n1):
+@pytest.mark.parametrize("n1,a", SPLITS)
+def test_four_step_layout_is_the_column_spectrum_order(n1, a):
     """C1 writes DFT_B output k1b of slab n1a to row k1b A + n1a; C2 turns the
     A rows k1b A + i into k1 = k1b + B k1a at row k1b A + k1a = prow(k1)."""
-    a, b = split(n1)
+    b = n1 // a
     rows = [prow(k1, a, b) for k1 in range(n1)]
     assert sorted(rows) == list(range(n1))
     for k1 in range(n1):

@@ -132,7 +132,7 @@ def test_tuned_multi_and_forced_families():
     xs = _inputs(shapes, 400)
     m = MultiPlan(shapes, tuned=True)
     fams = m.group_families()
-    assert len(fams) == 3 and all(f in ("seq", "pair", "fs2") for f in fams)
+    assert len(fams) == 3 and all(f in ("seq", "pair", "fs2") or f.startswith("fs2/") for f in fams)
     X = m.forward(m.pack([torch.from_numpy(x) for x in xs]))
     torch.cuda.synchronize()
     for x, Xi in zip(xs, m.unpack(X)):
@@ -157,7 +157,7 @@ def test_tune_cache_file_is_written_and_reused(tmp_path):
     code = ("import sys; sys.path.insert(0, %r)\n"
             "from paper_2110_01172_gb300 import Plan\n"
             "p = Plan((512, 512), batch=3, tuned=True)\n"
-            "print(p.family)\n") % ROOT
+            "print(p.choice)\n") % ROOT
     env = dict(os.environ, GBDCT_TUNE_CACHE=str(cache))
     first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert first.returncode == 0, first.stderr

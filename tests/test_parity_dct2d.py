@@ -200,6 +200,29 @@ def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
     plan.close()
 
 
+@pytest.mark.parametrize("shape,a", [((4096, 4096), 32), ((4096, 4096), 128), ((2048, 1024), 16),
+                                     ((2048, 1024), 128), ((8192, 512), 128), ((1024, 2048), 64),
+                                     ((512, 4096), 16), ((256, 16384), 16)])
+def test_every_four_step_split_matches_oracle(shape, a):
+    """The autotuner's tile candidates: the four-step family with each split
+    N1 = A * (N1 / A) of its column FFT, against the full oracle."""
+    from paper_2110_01172_gb300 import Plan
+    plan = Plan(shape, "dct2", family=f"fs2/{a}")
+    assert plan.family == "fs2"
+    _check_full(plan, shape, seed=17)
+    plan.close()
+
+
+def test_invalid_four_step_splits_are_rejected():
+    from paper_2110_01172_gb300 import GbdctError, Plan
+    with pytest.raises(GbdctError):
+        Plan((4096, 4096), family="fs2/16")    # B = 256 is out of range
+    with pytest.raises(GbdctError):
+        Plan((256, 256), family="fs2/32")      # B = 8 is out of range
+    with pytest.raises(GbdctError):
+        Plan((1024, 1024), family="fs2/48")    # not a supported factor
+
+
 @pytest.mark.parametrize("family", ["fs2"])
 def test_batched_four_step_families(family, monkeypatch):
     monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
