@@ -36,6 +36,7 @@
 
 #include "dct2d_kernels.cuh"
 #include "fft_soa.cuh"
+#include "l2_hint.cuh"
 
 #include <type_traits>
 
@@ -303,6 +304,9 @@ k_fs2_colv(Dct2dArgs a) {
   const int colv = blockIdx.y * C::NG + c;  // V index within a row
   V* W = reinterpret_cast<V*>(a.work + (long long)blockIdx.z * a.work_bstride);
 
+  // L2 policies: the streamed input / output evict first, the workspace
+  // (read again by the next launch of the transform) evicts last
+  const uint64_t pol_stream = l2::evict_first(), pol_keep = l2::evict_last();
   V x[T];
 #pragma unroll
   for (int j = 0; j < T; ++j) {
@@ -310,15 +314,15 @@ k_fs2_colv(Dct2dArgs a) {
     if constexpr (KIND == 0) {
       const float* xin = a.in + (long long)blockIdx.z * a.in_bstride;
       const int row = reorder_src(r + G::A * i, N1);
-      x[j] = reinterpret_cast<const V*>(xin + (long long)row * N2)[colv];
+      x[j] = l2::ld(reinterpret_cast<const V*>(xin + (long long)row * N2) + colv, pol_stream);
       if (a.vkind == 1) {  // DST-II: (-1)^(n1 + n2); real columns alternate in parity
         const float sr = (row & 1) ? -1.f : 1.f;
         x[j] = vsign(x[j], sr, -sr);
       }
     } else if constexpr (KIND == 3) {
-      x[j] = W[(long long)(i * G::A + r) * hv + colv];
+      x[j] = l2::ld(W + (long long)(i * G::A + r) * hv + colv, pol_stream);  // last use of the workspace
     } else {
-      x[j] = W[(long long)(r * G::A + i) * hv + colv];
+      x[j] = l2::ld(W + (long long)(r * G::A + i) * hv + colv, pol_keep);
     }
   }
   colv_dft<S, INV>(x, q, c, ex);
@@ -330,12 +334,12 @@ k_fs2_colv(Dct2dArgs a) {
       V y = x[i * Q + p];
       if constexpr (KIND == 0) {
         y = cmul(y, __ldg(a.fstw + r * G::B + o));
-        W[(long long)(o * G::A + r) * hv + colv] = y;
+        l2::st(W + (long long)(o * G::A + r) * hv + colv, y, pol_keep);
       } else if constexpr (KIND == 2) {
         y = cmulc(y, __ldg(a.fstw + o * G::B + r));
-        W[(long long)(r * G::A + o) * hv + colv] = y;
+        l2::st(W + (long long)(r * G::A + o) * hv + colv, y, pol_keep);
       } else if constexpr (KIND == 1) {
-        W[(long long)(r * G::A + o) * hv + colv] = y;
+        l2::st(W + (long long)(r * G::A + o) * hv + colv, y, pol_keep);
       } else {
         float* xo = a.out + (long long)blockIdx.z * a.out_bstride;
         const int row = reorder_src(r + G::A * o, N1);
@@ -344,7 +348,7 @@ k_fs2_colv(Dct2dArgs a) {
           const float sc = (a.vkind != 3) ? -sr : sr;
           y = vsign(y, sr, sc);
         }
-        reinterpret_cast<V*>(xo + (long long)row * N2)[colv] = y;
+        l2::st(reinterpret_cast<V*>(xo + (long long)row * N2) + colv, y, pol_stream);
       }
     }
 }
@@ -705,10 +709,11 @@ __device__ __forceinline__ void fwd_split_x2(const float2* __restrict__ za, cons
                                              bool packed, soa::C2* v) {
   constexpr int TPS = fft_tps(L);
   constexpr int MASK = mirror_lane_mask<TPS>();
+  const uint64_t pol = l2::evict_first();  // last use of the workspace
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int p = t + TPS * j;
-    const float2 A = za[p], Am = ma[p], B = zb[p], Bm = mb[p];
+    const float2 A = l2::ld(za + p, pol), Am = l2::ld(ma + p, pol), B = l2::ld(zb + p, pol), Bm = l2::ld(mb + p, pol);
     // low point n2 = p (this thread), high point L-1-p (the mirror lane)
     const float lra = packed ? A.x : A.x + Am.x, lia = packed ? Am.x : A.y - Am.y;
     const float hra = packed ? A.y : A.y + Am.y, hia = packed ? Am.y : Am.x - A.x;
@@ -741,6 +746,7 @@ __device__ __forceinline__ void fwd_post_x2(const float4* __restrict__ s, const 
   float* ya1 = y + (long long)(rev ? N1 - 1 - kma : kma) * L;
   float* yb0 = y + (long long)(rev ? N1 - 1 - (k1 + 1) : k1 + 1) * L;
   float* yb1 = y + (long long)(rev ? N1 - 1 - kmb : kmb) * L;
+  const uint64_t pol = l2::evict_first();  // the output is streamed out
   auto column = [&](int c) {
     const soa::C2 P = soa::unpack(s[soa::pidx4(c)]);
     const soa::C2 M = soa::unpack(s[soa::pidx4((L - c) & (L - 1))]);
@@ -755,15 +761,15 @@ __device__ __forceinline__ void fwd_post_x2(const float4* __restrict__ s, const 
     const soa::C2 sv = soa::mulw(u, soa::bc(bt.x), soa::bc(bt.y));
     const soa::C2 tv = soa::mulw(w, soa::bc(bt.x), soa::bc(bt.y));
     const int c0 = rev ? L - 1 - c : c, c1 = rev ? c - 1 : L - c;  // stored columns of c and L-c
-    ya0[c0] = sv.re.x;
-    yb0[c0] = sv.re.y;
-    ya1[c0] = -tv.im.x;
-    yb1[c0] = -tv.im.y;
+    l2::st(ya0 + c0, sv.re.x, pol);
+    l2::st(yb0 + c0, sv.re.y, pol);
+    l2::st(ya1 + c0, -tv.im.x, pol);
+    l2::st(yb1 + c0, -tv.im.y, pol);
     if (c != 0 && c != L / 2) {
-      ya0[c1] = -sv.im.x;
-      yb0[c1] = -sv.im.y;
-      ya1[c1] = -tv.re.x;
-      yb1[c1] = -tv.re.y;
+      l2::st(ya0 + c1, -sv.im.x, pol);
+      l2::st(yb0 + c1, -sv.im.y, pol);
+      l2::st(ya1 + c1, -tv.re.x, pol);
+      l2::st(yb1 + c1, -tv.re.y, pol);
     }
   };
 #pragma unroll 2
@@ -827,22 +833,22 @@ __device__ __forceinline__ InvRows inv_rows_of(const Dct2dArgs& a, const float* 
 
 // The four reads c1, c3, c4, c2 of point k2 of one item.
 template <int L, bool MAPPED>
-__device__ __forceinline__ float4 inv_reads(const InvRows& r, int k2, bool rev, bool swapc) {
+__device__ __forceinline__ float4 inv_reads(const InvRows& r, int k2, bool rev, bool swapc, uint64_t pol) {
   const int km = (L - k2) & (L - 1);
   float c1, c3, c4, c2;
   if constexpr (!MAPPED) {
-    c1 = r.ra ? r.ra[k2] : 0.f;
-    c3 = r.rb[k2];
-    c4 = (k2 && r.ra) ? r.ra[km] : 0.f;
-    c2 = k2 ? r.rb[km] : 0.f;
+    c1 = r.ra ? l2::ld(r.ra + k2, pol) : 0.f;
+    c3 = l2::ld(r.rb + k2, pol);
+    c4 = (k2 && r.ra) ? l2::ld(r.ra + km, pol) : 0.f;
+    c2 = k2 ? l2::ld(r.rb + km, pol) : 0.f;
   } else {
     const int ka = swapc ? km : k2, kb = swapc ? k2 : km;
     const int pa = rev ? L - 1 - ka : ka, pb = rev ? L - 1 - kb : kb;
     const bool z0 = swapc && !k2;
-    c1 = (!r.ra || z0) ? 0.f : r.ra[pa];
-    c3 = z0 ? 0.f : r.rb[pa];
-    c4 = (k2 && r.ra) ? r.ra[pb] : 0.f;
-    c2 = k2 ? r.rb[pb] : 0.f;
+    c1 = (!r.ra || z0) ? 0.f : l2::ld(r.ra + pa, pol);
+    c3 = z0 ? 0.f : l2::ld(r.rb + pa, pol);
+    c4 = (k2 && r.ra) ? l2::ld(r.ra + pb, pol) : 0.f;
+    c2 = k2 ? l2::ld(r.rb + pb, pol) : 0.f;
   }
   return make_float4(c1, c3, c4, c2);
 }
@@ -855,11 +861,12 @@ __device__ __forceinline__ void inv_pre_x2(const Dct2dArgs& a, const InvRows& A,
   const float2 iaA = __ldg(a.ia + k1), iaB = __ldg(a.ia + k1 + 1);
   const float2 ih = __ldg(a.ia + a.n1 / 2);
   const float2 iar = make_float2(iaA.x, iaB.x), iai = make_float2(iaA.y, iaB.y);
+  const uint64_t pol = l2::evict_first();  // the input is streamed in
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const int k2 = g + TPS * j;
-    const float4 ca = inv_reads<L, MAPPED>(A, k2, rev, swapc);
-    const float4 cb = inv_reads<L, MAPPED>(B, k2, rev, swapc);
+    const float4 ca = inv_reads<L, MAPPED>(A, k2, rev, swapc, pol);
+    const float4 cb = inv_reads<L, MAPPED>(B, k2, rev, swapc, pol);
     const float2 bk = __ldg(a.ib + k2);
     // x = (c1 - c2, -(c3 + c4)), v = x b ia
     const soa::C2 x{make_float2(ca.x - ca.w, cb.x - cb.w), make_float2(-(ca.y + ca.z), -(cb.y + cb.z))};
@@ -885,14 +892,15 @@ __device__ __forceinline__ void inv_pair_x2(const float4* __restrict__ s, const 
   float2* ma = Zw + (long long)fs2_prow(row_mirror(k1, a.n1), a.fsA, a.fsB) * (L / 2);
   float2* zb = Zw + (long long)fs2_prow(k1 + 1, a.fsA, a.fsB) * (L / 2);
   float2* mb = Zw + (long long)fs2_prow(row_mirror(k1 + 1, a.n1), a.fsA, a.fsB) * (L / 2);
+  const uint64_t pol = l2::evict_last();  // read again by the next column step
 #pragma unroll 2
   for (int r = 0; r < L / 2 / TPS; ++r) {
     const int p = g + TPS * r;
     const soa::C2 u = soa::unpack(s[soa::pidx4(p)]), w = soa::unpack(s[soa::pidx4(L - 1 - p)]);
-    zb[p] = make_float2(u.re.y - w.im.y, u.im.y + w.re.y);
-    mb[p] = make_float2(u.re.y + w.im.y, w.re.y - u.im.y);
-    za[p] = packed ? make_float2(u.re.x, w.re.x) : make_float2(u.re.x - w.im.x, u.im.x + w.re.x);
-    ma[p] = packed ? make_float2(u.im.x, w.im.x) : make_float2(u.re.x + w.im.x, w.re.x - u.im.x);
+    l2::st(zb + p, make_float2(u.re.y - w.im.y, u.im.y + w.re.y), pol);
+    l2::st(mb + p, make_float2(u.re.y + w.im.y, w.re.y - u.im.y), pol);
+    l2::st(za + p, packed ? make_float2(u.re.x, w.re.x) : make_float2(u.re.x - w.im.x, u.im.x + w.re.x), pol);
+    l2::st(ma + p, packed ? make_float2(u.im.x, w.im.x) : make_float2(u.re.x + w.im.x, w.re.x - u.im.x), pol);
   }
 }
 
