@@ -173,6 +173,14 @@ const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
  * GBDCT_ERR_TIMEOUT, GBDCT_ERR_INVALID_ARG (NULL plan) or GBDCT_ERR_CUDA. */
 gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan);
 
+/* Magnitude threshold of Section V-A (Eq. image-compression, the compression
+ * step of Algorithm 3), fused into the forward transform's last stores: every
+ * forward output X with |X| < eps (compared in FP32) is stored as zero.
+ * eps = 0 (the default) turns it off; the inverse is unaffected.  Supported for
+ * 2D plans of the four-step family ("fs2") with N2 <= 8192, else
+ * GBDCT_ERR_UNSUPPORTED; INVALID_ARG for a NULL plan or a negative or NaN eps. */
+gbdct_status gbdct_plan_set_threshold(gbdct_plan_t plan, float eps);
+
 /* Bound of every device-side wait of the plan's pipelined kernels, in polls of
  * the waited-on barrier (0, the default, is about half a second; a 3D plan
  * passes it to its 2D slices).  A diagnostic: a tiny bound makes the waits

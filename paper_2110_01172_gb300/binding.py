@@ -75,6 +75,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
             "gbdct_plan_kernel_family": (ctypes.c_char_p, [plan_p]),
             "gbdct_plan_check_device_error": (ctypes.c_int, [plan_p]),
             "gbdct_plan_set_wait_limit": (ctypes.c_int, [plan_p, ctypes.c_uint32]),
+            "gbdct_plan_set_threshold": (ctypes.c_int, [plan_p, ctypes.c_float]),
             "gbdct_exec_step": (ctypes.c_int, [plan_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
             "gbdct_plan_step_name": (ctypes.c_char_p, [plan_p, ctypes.c_int, ctypes.c_int]),
@@ -241,6 +242,11 @@ class Plan:
     def check_device_error(self) -> int:
         """Status of the device error word (OK, or ERR_TIMEOUT after a bounded wait gave up)."""
         return int(self._lib.gbdct_plan_check_device_error(self._h))
+
+    def set_threshold(self, eps: float):
+        """Forward outputs with |X| < eps stored as zero (Section V-A compression; 0: off)."""
+        _check(self._lib.gbdct_plan_set_threshold(self._h, float(eps)), "gbdct_plan_set_threshold")
+        return self
 
     def set_wait_limit(self, polls: int):
         """Bound of the plan's device-side waits in polls (0: the default)."""

@@ -747,6 +747,9 @@ __device__ __forceinline__ void fwd_post_x2(const float4* __restrict__ s, const 
   float* yb0 = y + (long long)(rev ? N1 - 1 - (k1 + 1) : k1 + 1) * L;
   float* yb1 = y + (long long)(rev ? N1 - 1 - kmb : kmb) * L;
   const uint64_t pol = l2::evict_first();  // the output is streamed out
+  // magnitude threshold of Section V-A, Eq. image-compression (0: off)
+  const float eps = a.thresh;
+  auto st = [&](float* p, float v) { l2::st(p, (eps > 0.f && fabsf(v) < eps) ? 0.f : v, pol); };
   auto column = [&](int c) {
     const soa::C2 P = soa::unpack(s[soa::pidx4(c)]);
     const soa::C2 M = soa::unpack(s[soa::pidx4((L - c) & (L - 1))]);
@@ -761,15 +764,15 @@ __device__ __forceinline__ void fwd_post_x2(const float4* __restrict__ s, const 
     const soa::C2 sv = soa::mulw(u, soa::bc(bt.x), soa::bc(bt.y));
     const soa::C2 tv = soa::mulw(w, soa::bc(bt.x), soa::bc(bt.y));
     const int c0 = rev ? L - 1 - c : c, c1 = rev ? c - 1 : L - c;  // stored columns of c and L-c
-    l2::st(ya0 + c0, sv.re.x, pol);
-    l2::st(yb0 + c0, sv.re.y, pol);
-    l2::st(ya1 + c0, -tv.im.x, pol);
-    l2::st(yb1 + c0, -tv.im.y, pol);
+    st(ya0 + c0, sv.re.x);
+    st(yb0 + c0, sv.re.y);
+    st(ya1 + c0, -tv.im.x);
+    st(yb1 + c0, -tv.im.y);
     if (c != 0 && c != L / 2) {
-      l2::st(ya0 + c1, -sv.im.x, pol);
-      l2::st(yb0 + c1, -sv.im.y, pol);
-      l2::st(ya1 + c1, -tv.re.x, pol);
-      l2::st(yb1 + c1, -tv.re.y, pol);
+      st(ya0 + c1, -sv.im.x);
+      st(yb0 + c1, -sv.im.y);
+      st(ya1 + c1, -tv.re.x);
+      st(yb1 + c1, -tv.re.y);
     }
   };
 #pragma unroll 2

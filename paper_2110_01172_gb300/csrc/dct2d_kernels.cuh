@@ -60,6 +60,7 @@ struct Dct2dArgs {
   int vkind;          // kind whose index/sign maps the fs2 kernels fold into their
                       // loads and stores (0: DCT-II, no map; see dct2d_fs2_kernels.cuh)
   const float4* tw2x; // stage twiddles for length N2 as (wr, wr, wi, wi) (fs2 two-item row passes)
+  float thresh;       // forward outputs with |X| < thresh stored as zero (0: off; fs2 two-item row pass)
   int nsm;            // host side only: multiprocessors of the device
 };
 

@@ -709,6 +709,13 @@ const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
   return plan->family == FAM_FS2 ? "fs2" : plan->family == FAM_PAIR ? "pair" : "seq";
 }
 
+gbdct_status gbdct_plan_set_threshold(gbdct_plan_t plan, float eps) {
+  if (!plan || !(eps >= 0.f)) return GBDCT_ERR_INVALID_ARG;
+  if (plan->ndim != 2 || plan->family != FAM_FS2 || plan->n2 > 8192) return GBDCT_ERR_UNSUPPORTED;
+  plan->args.thresh = eps;
+  return GBDCT_OK;
+}
+
 gbdct_status gbdct_plan_set_wait_limit(gbdct_plan_t plan, uint32_t polls) {
   if (!plan) return GBDCT_ERR_INVALID_ARG;
   if (plan->ndim == 3) return gbdct_plan_set_wait_limit(plan->inner, polls);

@@ -283,3 +283,43 @@ def test_single_steps_compose_to_the_full_transform(family, monkeypatch):
         plan.step(True, k, full, back)
     torch.cuda.synchronize()
     assert torch.equal(back, plan.inverse(full))
+
+
+@pytest.mark.parametrize("shape", [(256, 512), (1024, 1024), (2048, 4096)])
+def test_compression_threshold_fused_in_forward(shape):
+    """Section V-A, Eq. image-compression / Algorithm 3: the forward output with
+    |X| < eps stored as zero by the forward's last stores.  The GPU decision
+    is taken in FP32 on the same values as the unthresholded forward, so the
+    two agree bitwise; against the oracle's f_eps of the FP64 transform the
+    entries are compared away from the threshold, and D = IDCT(C) against the
+    oracle inverse of C."""
+    from paper_2110_01172_gb300 import Plan
+    x = inputs.gaussian_bumps(shape, seed=11)
+    xd = torch.from_numpy(x).cuda()
+    plan = Plan(shape)
+    X = plan.forward(xd).cpu().numpy()
+    ref = oracle.dct2_2d(x)
+    eps = np.float32(1e-3 * np.abs(ref).max())
+    plan.set_threshold(float(eps))
+    C = plan.forward(xd)
+    D = plan.inverse(C)
+    torch.cuda.synchronize()
+    Ch = C.cpu().numpy()
+    np.testing.assert_array_equal(Ch, np.where(np.abs(X) >= eps, X, np.float32(0)))
+    assert (Ch == 0).mean() > 0.1        # the threshold removes a real share of the spectrum
+    want = oracle.compress_threshold(ref, float(eps))
+    far = np.abs(np.abs(ref) - float(eps)) > MAX_ABS * np.abs(ref).max()
+    assert np.abs(Ch[far] - want[far]).max() <= MAX_ABS * np.abs(ref).max()
+    check(D.cpu().numpy(), oracle.idct2_2d(Ch))
+    plan.set_threshold(0.0)
+    again = plan.forward(xd)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(again.cpu().numpy(), X)
+
+
+def test_compression_threshold_rejections():
+    from paper_2110_01172_gb300 import GbdctError, Plan
+    with pytest.raises(GbdctError):
+        Plan((128, 128)).set_threshold(0.5)        # not a four-step plan
+    with pytest.raises(GbdctError):
+        Plan((256, 256)).set_threshold(-1.0)       # negative threshold
