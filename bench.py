@@ -51,7 +51,7 @@ FALLBACK_HBM_GBS = 6800.0
 # kernel sources with this digest; otherwise reported as null.
 TRAFFIC = {
     "sources_sha256": None,
-    "family": "fs2",
+    "family": "tp",
     "forward_bytes": None,
     "inverse_bytes": None,
 }
@@ -70,6 +70,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the secondary configurations")
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--family", default=None,
+                    help="force a kernel family for the headline plan (default: the plan's own choice)")
+    ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32",
+                    help="precision mode of the plan (--profile runs only)")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run W + K untimed steps of the plan (a fixed launch sequence for ncu captures)")
     return ap.parse_args(argv)
 
 
@@ -136,8 +142,9 @@ def measured_peaks():
 
 # Files that define the timed kernels of the default family (the ncu traffic in
 # TRAFFIC is valid only while these are unchanged).
-KERNEL_SOURCES = ("dct2d_fs2_kernels.cuh", "dct2d_kernels.cuh", "dct2d_launch.cuh", "fft_core.cuh",
-                  "fft_soa.cuh", "pass_fs2_cols.cu", "pass_fs2_rows.cu")
+KERNEL_SOURCES = ("dct2d_tp_kernels.cuh", "dct2d_fs2_kernels.cuh", "dct2d_kernels.cuh", "dct2d_launch.cuh",
+                  "fft_core.cuh", "fft_soa.cuh", "l2_hint.cuh", "tma_util.cuh", "pass_tp_cols.cu",
+                  "pass_tp_rows.cu")
 
 
 def sources_digest() -> str:
@@ -431,6 +438,22 @@ def run_configs(dev, peak):
                 "fwd_us": _event_loop_us(lambda i: plan.forward(xs[i % 2], ys[i % 2]), 20, stream),
                 "inv_us": _event_loop_us(lambda i: plan.inverse(xs[i % 2], ys[i % 2]), 20, stream)})
             plan.close()
+    # the two-pass family's tile candidates: column strips of NP column pairs
+    out["tp_strips"] = []
+    for shape in [(4096, 4096), (2048, 2048), (8192, 8192), (1024, 8192), (2048, 4096), (1024, 1024)]:
+        m = shape[0] // 2
+        for np_ in (1, 2, 4, 8, 16, 32):
+            thr, smem = np_ * (m // 16), np_ * (m + m // 16) * 16
+            if not (128 <= thr <= 512 and smem <= 227 * 1024 and (shape[1] // 4) % np_ == 0):
+                continue
+            plan = Plan(shape, family=f"tp/{np_}")
+            xs = [torch.rand(shape, device=dev) * 2 - 1 for _ in range(2)]
+            ys = [torch.empty_like(xs[0]) for _ in range(2)]
+            out["tp_strips"].append({
+                "shape": list(shape), "NP": np_, "threads": thr,
+                "fwd_us": _event_loop_us(lambda i: plan.forward(xs[i % 2], ys[i % 2]), 20, stream),
+                "inv_us": _event_loop_us(lambda i: plan.inverse(xs[i % 2], ys[i % 2]), 20, stream)})
+            plan.close()
     for kind in ("dst2", "idct_idxst", "idxst_idct"):
         out["kinds_2048"].append(one((2048, 2048), kind))
 
@@ -471,8 +494,35 @@ def run_configs(dev, peak):
     return out
 
 
+def run_profile(args):
+    """W + K forward/inverse steps of one plan with nothing else on the GPU,
+    so an ncu capture can address launches by position (2 or 3 launches per
+    transform, forward first)."""
+    import torch
+    from paper_2110_01172_gb300 import Plan, inputs
+    n1, n2 = args.n1, args.n2
+    plan = Plan((n1, n2), "dct2", family=args.family)
+    if args.precision != "fp32":
+        plan.set_precision(args.precision)
+    xs = [torch.from_numpy(inputs.uniform((n1, n2), seed=s)).cuda() for s in range(2)]
+    cs = [torch.empty_like(xs[0]) for _ in range(2)]
+    ys = [torch.empty_like(xs[0]) for _ in range(2)]
+    for i in range(args.warmup + args.steps):
+        plan.forward(xs[i % 2], cs[i % 2])
+        if args.precision == "fp32":
+            plan.inverse(cs[i % 2], ys[i % 2])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": True, "shape": [n1, n2], "family": plan.family, "precision": args.precision,
+                      "launches_per_transform": plan.launches_per_exec,
+                      "steps": args.warmup + args.steps}), flush=True)
+    plan.close()
+    return 0
+
+
 def run_ours(args):
     import torch
+    if args.profile:
+        return run_profile(args)
     rank, world, local = dist_init("nccl")
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA GPU (the library has no CPU path)")
@@ -481,7 +531,7 @@ def run_ours(args):
     from paper_2110_01172_gb300 import Plan, inputs
 
     n1, n2 = args.n1, args.n2
-    plan = Plan((n1, n2), "dct2")
+    plan = Plan((n1, n2), "dct2", family=args.family)
     stream = torch.cuda.current_stream(dev)
     x0 = torch.from_numpy(inputs.uniform((n1, n2), seed=0)).to(dev)
     xs = [x0] + [torch.from_numpy(inputs.uniform((n1, n2), seed=s)).to(dev) for s in range(1, NBUF)]

@@ -97,9 +97,9 @@ const char* gbdct_version(void);
  *         65535, else GBDCT_ERR_UNSUPPORTED.  ndim 1 gives UNSUPPORTED.
  *   dims  ndim sizes; each must be a power of two between 2 and 16384, else
  *         GBDCT_ERR_UNSUPPORTED (dims <= 0 give GBDCT_ERR_INVALID_ARG).
- *   kind  a gbdct_kind; dtype must be GBDCT_F32.  In the four-step family
- *         (fs2) the index/sign maps of the other kinds are folded into the
- *         first loads and last stores of the DCT-II kernels; the other
+ *   kind  a gbdct_kind; dtype must be GBDCT_F32.  In the two-pass (tp) and
+ *         four-step (fs2) families the index/sign maps of the other kinds are
+ *         folded into the first loads and last stores of the DCT-II kernels; the other
  *         families run the DCT-II kernels between two index/sign map kernels
  *         and own an extra staging array of batch*N1*N2 floats.
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises the device.
@@ -155,13 +155,14 @@ size_t gbdct_plan_workspace_bytes(gbdct_plan_t plan);
 /* Number of kernel launches one exec call issues (0 for a NULL plan). */
 int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
 
-/* Name of the kernel family the plan runs ("seq", "pair" or "fs2"; "" for a
- * NULL plan).  Every family computes the same transform; the plan picks the
- * fastest one that supports the shape (fs2: N1 in 256..8192 and N2 in
- * 256..16384; pair: both sides in 16..8192; seq: any supported size), and the
- * environment variable GBDCT_KERNEL_FAMILY=seq|pair|fs2, read at plan
- * creation, forces a family when it supports the shape (for testing and
- * comparison). */
+/* Name of the kernel family the plan runs ("seq", "pair", "fs2" or "tp"; ""
+ * for a NULL plan).  Every family computes the same transform; the plan picks
+ * the fastest one that supports the shape (tp: N1 in 512..8192 and N2 in
+ * 256..8192, two launches per direction; fs2: N1 in 256..8192 and N2 in
+ * 256..16384, three launches; pair: both sides in 16..8192; seq: any
+ * supported size), and the environment variable
+ * GBDCT_KERNEL_FAMILY=seq|pair|fs2|tp, read at plan creation, forces a family
+ * when it supports the shape (for testing and comparison). */
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan);
 
 /* Reports (and clears) a failure recorded on the device by the plan's
@@ -177,7 +178,8 @@ gbdct_status gbdct_plan_check_device_error(gbdct_plan_t plan);
  * step of Algorithm 3), fused into the forward transform's last stores: every
  * forward output X with |X| < eps (compared in FP32) is stored as zero.
  * eps = 0 (the default) turns it off; the inverse is unaffected.  Supported for
- * 2D plans of the four-step family ("fs2") with N2 <= 8192, else
+ * 2D plans of the two-pass ("tp") and four-step ("fs2") families with
+ * N2 <= 8192, else
  * GBDCT_ERR_UNSUPPORTED; INVALID_ARG for a NULL plan or a negative or NaN eps. */
 gbdct_status gbdct_plan_set_threshold(gbdct_plan_t plan, float eps);
 
@@ -194,8 +196,9 @@ gbdct_status gbdct_plan_destroy(gbdct_plan_t plan);
 
 /*
  * As gbdct_plan_create_batched with the kernel family named by `family`
- * ("seq", "pair" or "fs2"; every family computes the same
- * transform).  Errors: INVALID_ARG (NULL or unknown name, and the checks of
+ * ("seq", "pair", "fs2", "tp", or "fs2/<A>" for the four-step family with
+ * the column split N1 = A * (N1 / A), A and N1 / A in {16, 32, 64, 128}; every
+ * family computes the same transform).  Errors: INVALID_ARG (NULL or unknown name, and the checks of
  * gbdct_plan_create_batched), UNSUPPORTED when that family does not support
  * the shape, OOM, CUDA.  For a 3D plan the family applies to its 2D slices.
  */

@@ -146,7 +146,7 @@ class Plan:
 
     def __init__(self, shape, kind: str = "dct2", batch: int = 1, device=None, family: str | None = None,
                  tuned: bool = False):
-        """family: force a kernel family ("seq", "pair", "fs2");
+        """family: force a kernel family ("seq", "pair", "fs2", "tp", or "fs2/<A>");
         tuned: pick the fastest family by timing (gbdct_plan_create_tuned)."""
         torch = _torch()
         lib = load()
@@ -232,7 +232,7 @@ class Plan:
     def step(self, inverse: bool, step: int, x, out, stream=None):
         """Run launch `step` of the forward/inverse sequence alone (per-kernel timing)."""
         _check(self._lib.gbdct_exec_step(self._h, int(bool(inverse)), int(step), ctypes.c_void_p(x.data_ptr()),
-                                         ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, x.device)),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, self.device)),
                "gbdct_exec_step")
         return out
 
@@ -339,7 +339,7 @@ class MultiPlan:
             raise ValueError(f"expected a contiguous CUDA float32 buffer of {self.total} values")
         out = torch.empty_like(x) if out is None else out
         _check(self._lib.gbdct_multi_exec(self._h, int(inverse), ctypes.c_void_p(x.data_ptr()),
-                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, x.device)),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, self.device)),
                "gbdct_multi_exec")
         return out
 

@@ -314,15 +314,15 @@ k_fs2_colv(Dct2dArgs a) {
     if constexpr (KIND == 0) {
       const float* xin = a.in + (long long)blockIdx.z * a.in_bstride;
       const int row = reorder_src(r + G::A * i, N1);
-      x[j] = l2::ld(reinterpret_cast<const V*>(xin + (long long)row * N2) + colv, pol_stream);
+      x[j] = l2::ld_once(reinterpret_cast<const V*>(xin + (long long)row * N2) + colv, pol_stream);
       if (a.vkind == 1) {  // DST-II: (-1)^(n1 + n2); real columns alternate in parity
         const float sr = (row & 1) ? -1.f : 1.f;
         x[j] = vsign(x[j], sr, -sr);
       }
     } else if constexpr (KIND == 3) {
-      x[j] = l2::ld(W + (long long)(i * G::A + r) * hv + colv, pol_stream);  // last use of the workspace
+      x[j] = l2::ld_once(W + (long long)(i * G::A + r) * hv + colv, pol_stream);  // last use of the workspace
     } else {
-      x[j] = l2::ld(W + (long long)(r * G::A + i) * hv + colv, pol_keep);
+      x[j] = l2::ld_once(W + (long long)(r * G::A + i) * hv + colv, pol_keep);
     }
   }
   colv_dft<S, INV>(x, q, c, ex);
@@ -703,6 +703,20 @@ constexpr int mirror_lane_mask() { return TPS >= 32 ? 16 : TPS - 1; }
 // both the low value and the high value it implies (for point L-1-n2, which
 // belongs to the mirror butterfly TPS-1-t at j' = 15 - j), and the two mirror
 // lanes swap the high values.
+// Split of point p for both lanes from the column-spectrum values A = z_a(p),
+// Am = m_a(p), B = z_b(p), Bm = m_b(p): the low value (point p) into lo, the
+// high value (point L-1-p) exchanged with the mirror lane into hi.
+template <int MASK>
+__device__ __forceinline__ void split_point(float2 A, float2 Am, float2 B, float2 Bm, bool packed, soa::C2& lo,
+                                            soa::C2& hi) {
+  const float lra = packed ? A.x : A.x + Am.x, lia = packed ? Am.x : A.y - Am.y;
+  const float hra = packed ? A.y : A.y + Am.y, hia = packed ? Am.y : Am.x - A.x;
+  lo = soa::C2{make_float2(lra, B.x + Bm.x), make_float2(lia, B.y - Bm.y)};
+  const float h0 = hra, h1 = B.y + Bm.y, h2 = hia, h3 = Bm.x - B.x;
+  hi = soa::C2{make_float2(__shfl_xor_sync(0xffffffffu, h0, MASK), __shfl_xor_sync(0xffffffffu, h1, MASK)),
+               make_float2(__shfl_xor_sync(0xffffffffu, h2, MASK), __shfl_xor_sync(0xffffffffu, h3, MASK))};
+}
+
 template <int L>
 __device__ __forceinline__ void fwd_split_x2(const float2* __restrict__ za, const float2* __restrict__ ma,
                                              const float2* __restrict__ zb, const float2* __restrict__ mb, int t,
@@ -713,14 +727,10 @@ __device__ __forceinline__ void fwd_split_x2(const float2* __restrict__ za, cons
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int p = t + TPS * j;
-    const float2 A = l2::ld(za + p, pol), Am = l2::ld(ma + p, pol), B = l2::ld(zb + p, pol), Bm = l2::ld(mb + p, pol);
+    const float2 A = l2::ld_once(za + p, pol), Am = l2::ld_once(ma + p, pol), B = l2::ld_once(zb + p, pol),
+                 Bm = l2::ld_once(mb + p, pol);
     // low point n2 = p (this thread), high point L-1-p (the mirror lane)
-    const float lra = packed ? A.x : A.x + Am.x, lia = packed ? Am.x : A.y - Am.y;
-    const float hra = packed ? A.y : A.y + Am.y, hia = packed ? Am.y : Am.x - A.x;
-    v[j] = soa::C2{make_float2(lra, B.x + Bm.x), make_float2(lia, B.y - Bm.y)};
-    const float h0 = hra, h1 = B.y + Bm.y, h2 = hia, h3 = Bm.x - B.x;
-    v[15 - j] = soa::C2{make_float2(__shfl_xor_sync(0xffffffffu, h0, MASK), __shfl_xor_sync(0xffffffffu, h1, MASK)),
-                        make_float2(__shfl_xor_sync(0xffffffffu, h2, MASK), __shfl_xor_sync(0xffffffffu, h3, MASK))};
+    split_point<MASK>(A, Am, B, Bm, packed, v[j], v[15 - j]);
   }
 }
 
@@ -730,29 +740,29 @@ __device__ __forceinline__ void fwd_split_x2(const float2* __restrict__ za, cons
 // t = b w (b/2 in the table): y(k1,c) = Re s, y(kmir,c) = -Im t,
 // y(k1,L-c) = -Im s, y(kmir,L-c) = -Re t.  Packed lane a: a = 1 for row 0
 // and w = sqrt(1/2) (M.x - P.x, -(P.y + M.y)) for row N1/2.
-template <int L>
+template <int L, int ST = 1>
 __device__ __forceinline__ void fwd_post_x2(const float4* __restrict__ s, const Dct2dArgs& a, float* y, int k1,
-                                            bool packed, int g) {
+                                            int kb, bool packed, int g) {
   constexpr int TPS = fft_tps(L);
   constexpr float RH = 0.70710678118654752f;
   const int N1 = a.n1;
-  const float2 fa0 = __ldg(a.fa + k1), fa1 = __ldg(a.fa + k1 + 1);
+  const float2 fa0 = __ldg(a.fa + k1), fa1 = __ldg(a.fa + kb);
   // 1/2 of the split folded into the a-twiddle (not for the packed item)
   const float2 avr = make_float2(packed ? 1.f : 0.5f * fa0.x, 0.5f * fa1.x);
   const float2 avi = make_float2(packed ? 0.f : 0.5f * fa0.y, 0.5f * fa1.y);
   const bool rev = a.vkind == 1;  // DST-II: output (k1, k2) goes to (N1-1-k1, N2-1-k2)
-  const int kma = row_mirror(k1, N1), kmb = row_mirror(k1 + 1, N1);
+  const int kma = row_mirror(k1, N1), kmb = row_mirror(kb, N1);
   float* ya0 = y + (long long)(rev ? N1 - 1 - k1 : k1) * L;
   float* ya1 = y + (long long)(rev ? N1 - 1 - kma : kma) * L;
-  float* yb0 = y + (long long)(rev ? N1 - 1 - (k1 + 1) : k1 + 1) * L;
+  float* yb0 = y + (long long)(rev ? N1 - 1 - kb : kb) * L;
   float* yb1 = y + (long long)(rev ? N1 - 1 - kmb : kmb) * L;
   const uint64_t pol = l2::evict_first();  // the output is streamed out
   // magnitude threshold of Section V-A, Eq. image-compression (0: off)
   const float eps = a.thresh;
   auto st = [&](float* p, float v) { l2::st(p, (eps > 0.f && fabsf(v) < eps) ? 0.f : v, pol); };
   auto column = [&](int c) {
-    const soa::C2 P = soa::unpack(s[soa::pidx4(c)]);
-    const soa::C2 M = soa::unpack(s[soa::pidx4((L - c) & (L - 1))]);
+    const soa::C2 P = soa::unpack(s[ST * soa::pidx4(c)]);
+    const soa::C2 M = soa::unpack(s[ST * soa::pidx4((L - c) & (L - 1))]);
     const soa::C2 aP = soa::mulw(P, avr, avi), aM = soa::mulw(M, avr, avi);
     const soa::C2 u{soa::add2(aP.re, aM.re), soa::sub2(aP.im, aM.im)};
     soa::C2 w{soa::sub2(aP.re, aM.re), soa::add2(aP.im, aM.im)};
@@ -798,7 +808,7 @@ __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB) k_f
   soa::first_stage<L, false>(v, s, t);
   __syncthreads();
   soa::stages<L, 16, false>(s, g, a.tw2x);
-  fwd_post_x2<L>(s, a, a.out + (long long)blockIdx.z * a.out_bstride, k1, packed, g);
+  fwd_post_x2<L>(s, a, a.out + (long long)blockIdx.z * a.out_bstride, k1, k1 + 1, packed, g);
 }
 
 // Inverse four-read preprocess (Eq. 2d_idct_pre, conjugated twiddle, 1/(N1 N2)
@@ -857,16 +867,20 @@ __device__ __forceinline__ float4 inv_reads(const InvRows& r, int k2, bool rev, 
 }
 
 template <int L, bool MAPPED, bool PACKED>
-__device__ __forceinline__ void inv_pre_x2(const Dct2dArgs& a, const InvRows& A, const InvRows& B, int k1, int g,
-                                           soa::C2* v) {
+__device__ __forceinline__ void inv_pre_x2(const Dct2dArgs& a, const InvRows& A, const InvRows& B, int k1, int kb,
+                                           int g, soa::C2* v) {
   constexpr int TPS = fft_tps(L);
   const bool rev = MAPPED && a.vkind == 1, swapc = MAPPED && a.vkind == 2;
-  const float2 iaA = __ldg(a.ia + k1), iaB = __ldg(a.ia + k1 + 1);
+  const float2 iaA = __ldg(a.ia + k1), iaB = __ldg(a.ia + kb);
   const float2 ih = __ldg(a.ia + a.n1 / 2);
   const float2 iar = make_float2(iaA.x, iaB.x), iai = make_float2(iaA.y, iaB.y);
   const uint64_t pol = l2::evict_first();  // the input is streamed in
+  // points j and 15 - j back to back: the value read at N2 - k2 is read again
+  // as the k2 point of the mirror thread TPS - g at iteration 15 - j, so the
+  // two reads of every input value fall close together and the second hits L1
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int jj = 0; jj < 16; ++jj) {
+    const int j = (jj & 1) ? 15 - (jj >> 1) : (jj >> 1);
     const int k2 = g + TPS * j;
     const float4 ca = inv_reads<L, MAPPED>(A, k2, rev, swapc, pol);
     const float4 cb = inv_reads<L, MAPPED>(B, k2, rev, swapc, pol);
@@ -921,9 +935,9 @@ __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB_INV)
   const bool packed = (k1 == 0);
   soa::C2 v[16];
   if (packed)
-    inv_pre_x2<L, MAPPED, true>(a, A, B, k1, g, v);
+    inv_pre_x2<L, MAPPED, true>(a, A, B, k1, k1 + 1, g, v);
   else
-    inv_pre_x2<L, MAPPED, false>(a, A, B, k1, g, v);
+    inv_pre_x2<L, MAPPED, false>(a, A, B, k1, k1 + 1, g, v);
   soa::first_stage<L, true>(v, s, g);
   __syncthreads();
   soa::stages<L, 16, true>(s, g, a.tw2x);

@@ -59,8 +59,13 @@ struct Dct2dArgs {
   int fsA, fsB;       // four-step split N1 = A * B (four-step families)
   int vkind;          // kind whose index/sign maps the fs2 kernels fold into their
                       // loads and stores (0: DCT-II, no map; see dct2d_fs2_kernels.cuh)
-  const float4* tw2x; // stage twiddles for length N2 as (wr, wr, wi, wi) (fs2 two-item row passes)
-  float thresh;       // forward outputs with |X| < thresh stored as zero (0: off; fs2 two-item row pass)
+  const float4* tw2x; // stage twiddles for length N2 as (wr, wr, wi, wi) (two-item row passes)
+  float thresh;       // forward outputs with |X| < thresh stored as zero (0: off; two-item row passes)
+  const float4* tw1x; // stage twiddles for length N1/2 as (wr, wr, wi, wi) (two-pass column passes)
+  const float2* r2w;  // W_N1^k = exp(-2 pi i k / N1), k in [0, N1/2] (two-pass family's radix-2 step)
+  int tpNP;           // strip width of the two-pass column pass in column pairs (0: the default)
+  uint32_t polls;     // bound of device-side waits in polls (0: the default)
+  int io_dev;         // host side only: input and output are device memory (bulk tensor copies allowed)
   int nsm;            // host side only: multiprocessors of the device
 };
 

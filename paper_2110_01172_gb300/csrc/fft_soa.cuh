@@ -51,6 +51,9 @@ __device__ __forceinline__ C2 mul_mj(C2 a) {
 }
 
 __device__ __forceinline__ float4 pack(C2 a) { return make_float4(a.re.x, a.re.y, a.im.x, a.im.y); }
+// The two points as two interleaved complex values (re_a, im_a, re_b, im_b),
+// the layout of a pair of adjacent complex columns in global memory.
+__device__ __forceinline__ float4 pack_aos(C2 a) { return make_float4(a.re.x, a.im.x, a.re.y, a.im.y); }
 __device__ __forceinline__ C2 unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
 
 // Multiply by W16^E = exp(-+2 pi i E / 16) for a compile-time E.
@@ -164,9 +167,10 @@ __device__ __forceinline__ C2 apply(C2 u, C2 w) {
 }
 
 // u[j] *= w^j (conjugated for the inverse), j = 1 .. R-1, where entry (j-1)*NS
-// of twp is w^j.  For R = 16 only w, w^2, w^4 and w^8 are read; the other
-// powers are products of at most three of them (a few ulp from the exactly
-// rounded values), which keeps the table reads (and registers) low.
+// of twp is w^j.  Only the power-of-two powers are read (w, w^2, w^4, w^8 for
+// R = 16); the other powers are products of at most three of them (a few ulp
+// from the exactly rounded values), which keeps the table reads (and
+// registers) low.
 template <int R, bool INV>
 __device__ __forceinline__ void twiddle(C2* u, const float4* __restrict__ twp, int NS) {
   if constexpr (R == 16) {
@@ -189,6 +193,21 @@ __device__ __forceinline__ void twiddle(C2* u, const float4* __restrict__ twp, i
     u[13] = apply<INV>(u[13], wmul(w1, w12));
     u[14] = apply<INV>(u[14], wmul(w2, w12));
     u[15] = apply<INV>(u[15], wmul(w7, w8));
+  } else if constexpr (R == 8) {  // w, w^2, w^4 read; the rest are their products
+    const C2 w1 = ldw(twp), w2 = ldw(twp + NS), w4 = ldw(twp + 3 * NS);
+    const C2 w3 = wmul(w1, w2);
+    u[1] = apply<INV>(u[1], w1);
+    u[2] = apply<INV>(u[2], w2);
+    u[3] = apply<INV>(u[3], w3);
+    u[4] = apply<INV>(u[4], w4);
+    u[5] = apply<INV>(u[5], wmul(w1, w4));
+    u[6] = apply<INV>(u[6], wmul(w2, w4));
+    u[7] = apply<INV>(u[7], wmul(w3, w4));
+  } else if constexpr (R == 4) {
+    const C2 w1 = ldw(twp), w2 = ldw(twp + NS);
+    u[1] = apply<INV>(u[1], w1);
+    u[2] = apply<INV>(u[2], w2);
+    u[3] = apply<INV>(u[3], wmul(w1, w2));
   } else {
 #pragma unroll
     for (int j = 1; j < R; ++j) u[j] = apply<INV>(u[j], ldw(twp + (j - 1) * NS));
@@ -196,18 +215,35 @@ __device__ __forceinline__ void twiddle(C2* u, const float4* __restrict__ twp, i
 }
 
 // First stage from registers: v holds points g + j (L/16) of both sequences;
-// radix-16 DFT, outputs g*16 + m stored to s.
-template <int L, bool INV>
+// radix-16 DFT, outputs g*16 + m stored to s.  Point i of the sequence pair
+// lives at s[ST * pidx4(i)]: ST > 1 interleaves ST sequence pairs point by
+// point (the column passes of the two-pass family, whose warps span pairs).
+template <int L, bool INV, int ST = 1>
 __device__ __forceinline__ void first_stage(C2* v, float4* __restrict__ s, int g) {
   constexpr int R = stage_radix(L, 1);
   dft<R, INV>(v);
 #pragma unroll
-  for (int m = 0; m < R; ++m) s[pidx4(g * R + m)] = pack(v[m]);
+  for (int m = 0; m < R; ++m) s[ST * pidx4(g * R + m)] = pack(v[m]);
+}
+
+// Shared-memory slot of output point k of the last stage: OUT = 0 the padded
+// layout (pidx4), OUT = 1 dense (k), OUT = 2 dense with the upper half
+// reversed (L/2 + (L-1-k) for k >= L/2), the order in which a bulk tensor
+// store writes the rows of the two reorder residues.  Consecutive k of a
+// stage's last writes stay on distinct banks in all three.  The dense forms
+// are read by bulk tensor stores, so their slots hold the global-memory
+// layout (pack_aos) instead of the engine's two-lane layout (pack).
+template <int L, int OUT>
+__device__ __forceinline__ int out_slot(int k) {
+  if constexpr (OUT == 0) return pidx4(k);
+  else if constexpr (OUT == 1) return k;
+  else return k < L / 2 ? k : (3 * L / 2 - 1 - k);
 }
 
 // Stages NS .. L through shared memory (natural order in and out); every
-// thread of the CTA calls this (it contains __syncthreads).
-template <int L, int NS, bool INV>
+// thread of the CTA calls this (it contains __syncthreads).  The last stage
+// writes its outputs at out_slot<L, OUT>.
+template <int L, int NS, bool INV, int ST = 1, int OUT = 0>
 __device__ __forceinline__ void stages(float4* __restrict__ s, int g, const float4* __restrict__ tw) {
   if constexpr (NS < L) {
     constexpr int R = stage_radix(L, NS);
@@ -220,7 +256,7 @@ __device__ __forceinline__ void stages(float4* __restrict__ s, int g, const floa
     for (int q = 0; q < NB; ++q) {
       const int t = g + q * TPS;
 #pragma unroll
-      for (int j = 0; j < R; ++j) v[q * R + j] = unpack(s[pidx4(t + j * STRIDE)]);
+      for (int j = 0; j < R; ++j) v[q * R + j] = unpack(s[ST * pidx4(t + j * STRIDE)]);
     }
     __syncthreads();
 #pragma unroll
@@ -230,11 +266,17 @@ __device__ __forceinline__ void stages(float4* __restrict__ s, int g, const floa
       const int k = t & (NS - 1);
       twiddle<R, INV>(u, tw + tw_offset(L, NS) + k, NS);
       dft<R, INV>(u);
+      if constexpr (NS * R < L) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) s[pidx4(stage_out_index<L, NS>(t, m))] = pack(u[m]);
+        for (int m = 0; m < R; ++m) s[ST * pidx4(stage_out_index<L, NS>(t, m))] = pack(u[m]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < R; ++m)
+          s[ST * out_slot<L, OUT>(stage_out_index<L, NS>(t, m))] = OUT ? pack_aos(u[m]) : pack(u[m]);
+      }
     }
     __syncthreads();
-    stages<L, NS * R, INV>(s, g, tw);
+    stages<L, NS * R, INV, ST, OUT>(s, g, tw);
   }
 }
 

@@ -48,11 +48,27 @@ struct gbdct_plan_s {
 namespace {
 
 // Kernel families (all compute the same transform; chosen by size):
-//   FAM_FS2  four-step column steps + two-item row passes,
+//   FAM_TP   two passes per direction: half-length column FFTs on strips +
+//            row passes with the radix-2 column step folded in,
+//            N1 in {512..8192}, N2 in {256..8192}
+//   FAM_FS2  four-step column steps + two-item row passes (three passes),
 //            N1 in {256..8192}, N2 in {256..16384}
 //   FAM_PAIR two interleaved sequences per thread, 16 <= N1, N2 <= 8192
 //   FAM_SEQ  one sequence per thread group, any supported size
-enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_FS2 = 5 };
+enum { FAM_SEQ = 0, FAM_PAIR = 1, FAM_FS2 = 5, FAM_TP = 6 };
+
+// Families whose kernels fold the other kinds' index/sign maps into their
+// loads and stores (no map kernels, no staging array).
+bool folds_maps(int family) { return family == FAM_FS2 || family == FAM_TP; }
+
+// Radix-2 twiddles of the two-pass family: out[k] = W_N1^k, k in [0, N1/2], FP64.
+__global__ void k_gen_r2_twiddles(float2* out, int n1) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > n1 / 2) return;
+  double sn, cs;
+  sincospi(-2.0 * (double)k / (double)n1, &sn, &cs);
+  out[k] = make_float2((float)cs, (float)sn);
+}
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int64_t v) {
@@ -189,22 +205,25 @@ struct DeviceGuard {
 // memory when the device can access pageable memory.  While `s` is capturing
 // a graph the check is skipped (the pointers of a captured launch are the
 // caller's own device buffers, and the query is not needed there).
-bool device_accessible(const void* ptr, int device, cudaStream_t s) {
+// Returns 0 (not accessible), 1 (this device's memory) or 2 (accessible
+// otherwise); *is_dev tells the kernels whether bulk tensor copies may be used.
+enum { PTR_NONE = 0, PTR_DEVICE = 1, PTR_OTHER = 2 };
+int pointer_kind(const void* ptr, int device, cudaStream_t s) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) return true;
+  if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) return PTR_DEVICE;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return PTR_NONE;
   }
   switch (at.type) {
-    case cudaMemoryTypeDevice: return at.device == device;
-    case cudaMemoryTypeManaged: return true;
-    case cudaMemoryTypeHost: return at.devicePointer == ptr;
+    case cudaMemoryTypeDevice: return at.device == device ? PTR_DEVICE : PTR_NONE;
+    case cudaMemoryTypeManaged: return PTR_OTHER;
+    case cudaMemoryTypeHost: return at.devicePointer == ptr ? PTR_OTHER : PTR_NONE;
     default: {
       int pageable = 0;
       cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
-      return pageable != 0;
+      return pageable != 0 ? PTR_OTHER : PTR_NONE;
     }
   }
 }
@@ -351,17 +370,25 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
     if (dims[i] <= 0) return GBDCT_ERR_INVALID_ARG;
   if (kind < GBDCT_DCT2 || kind > GBDCT_IDXST_IDCT) return GBDCT_ERR_INVALID_ARG;
   if (dtype != GBDCT_F32) return GBDCT_ERR_UNSUPPORTED;
-  // a family name, or "fs2/<A>" for the four-step family with the split
-  // N1 = A * (N1 / A) of its column FFT (A and N1 / A in {16, 32, 64, 128})
+  // a family name, "fs2/<A>" for the four-step family with the split
+  // N1 = A * (N1 / A) of its column FFT (A and N1 / A in {16, 32, 64, 128}),
+  // or "tp/<NP>" for the two-pass family with column strips of NP column pairs
   const char* fname = force ? force : getenv("GBDCT_KERNEL_FAMILY");
-  int split_a = 0;
+  int split_a = 0, strip_np = 0;
   if (fname && strncmp(fname, "fs2/", 4) == 0) {
     split_a = atoi(fname + 4);
     if (split_a != 16 && split_a != 32 && split_a != 64 && split_a != 128) split_a = -1;
   }
-  if (force && (split_a < 0 || (!split_a && strcmp(force, "seq") && strcmp(force, "pair") && strcmp(force, "fs2"))))
+  if (fname && strncmp(fname, "tp/", 3) == 0) {
+    strip_np = atoi(fname + 3);
+    if (strip_np < 1 || strip_np > 32 || (strip_np & (strip_np - 1))) strip_np = -1;
+  }
+  if (force && (split_a < 0 || strip_np < 0 ||
+                (!split_a && !strip_np && strcmp(force, "seq") && strcmp(force, "pair") && strcmp(force, "fs2") &&
+                 strcmp(force, "tp"))))
     return GBDCT_ERR_INVALID_ARG;
   if (split_a < 0) split_a = 0;
+  if (strip_np < 0) strip_np = 0;
   if (ndim == 3) return create_3d(out, dims, batch, kind, dtype, force);
   if (ndim != 2) return GBDCT_ERR_UNSUPPORTED;
   for (int i = 0; i < ndim; ++i) {
@@ -391,10 +418,16 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
                     p->lg2 >= gbdct::kPairMinLog2 && p->lg2 <= gbdct::kPairMaxLog2;
   const bool fs2 = p->lg1 >= gbdct::kFs2MinLog2N1 && p->lg1 <= gbdct::kFs2MaxLog2N1 &&
                    p->lg2 >= gbdct::kFs2MinLog2N2 && p->lg2 <= gbdct::kFs2MaxLog2N2;
-  // Default: the occupancy-first four-step family where it applies, else the
-  // two-sequence family, else one sequence per thread group (fastest measured
-  // at every shape they share).
-  p->family = fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
+  const bool tp = p->lg1 >= gbdct::kTpMinLog2N1 && p->lg1 <= gbdct::kTpMaxLog2N1 &&
+                  p->lg2 >= gbdct::kTpMinLog2N2 && p->lg2 <= gbdct::kTpMaxLog2N2;
+  // a strip width the two-pass column pass is built for at this shape
+  const bool tp_np_ok = tp && strip_np > 0 && gbdct::tp_strip_ok(n1 / 2, n2, strip_np);
+  // Default: the two-pass family for N1 <= 4096, the four-step family where
+  // it applies, else the two-sequence family, else one sequence per thread
+  // group (fastest measured at every shape they share; at N1 = 8192 the
+  // four-step column steps beat the two-pass column pass's 16 KB-per-pair
+  // strips).
+  p->family = (tp && p->lg1 <= 12) ? FAM_TP : fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
   // GBDCT_KERNEL_FAMILY=seq|pair|fs2 forces a family when it supports the shape
   // (used to test and compare every kernel family on the same inputs).
   if (const char* f = fname) {
@@ -403,6 +436,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
     if (!strcmp(f, "seq")) chosen = FAM_SEQ;
     else if (!strcmp(f, "pair") && pair) chosen = FAM_PAIR;
     else if (!strcmp(f, "fs2") && fs2) chosen = FAM_FS2;
+    else if (!strcmp(f, "tp") && tp) chosen = FAM_TP;
+    else if (strip_np && tp_np_ok) chosen = FAM_TP;
     else if (split_a && fs2 && n1 / split_a >= 16 && n1 / split_a <= 128) chosen = FAM_FS2;
     if (chosen < 0 && force) {
       delete p;
@@ -410,7 +445,13 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
     }
     p->family = chosen < 0 ? before : chosen;
   }
-  const bool four_step = p->family == FAM_FS2;
+  const bool two_pass = p->family == FAM_TP;
+  // a two-pass plan also carries the four-step configuration: full transforms
+  // on host-mapped buffers run the four-step kernels, whose first and last
+  // launches read and write whole 1 KB row segments (the two-pass column
+  // pass's 32-byte row pieces cross the host link poorly)
+  const bool four_step = p->family == FAM_FS2 || two_pass;
+  const bool two_item_rows = four_step || two_pass;  // row passes on the SoA engine (float4 twiddles)
   p->pmax = 16;
 
   // Table layout, each block padded to 2 float2 (16 B).
@@ -420,8 +461,13 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   const size_t ta = round_up(n1 / 2 + 1, 2);
   const size_t tb = round_up(n2, 2);
   const size_t tf = four_step ? round_up(n1, 2) : 0;
-  const size_t tx = four_step ? 2 * t2 : 0;  // float4 copy of the N2 stage twiddles
-  p->table_elems = t1 + t2 + 2 * ta + 2 * tb + tf + tx + 2;  // + 16 bytes for the error word
+  const size_t tx = two_item_rows ? 2 * t2 : 0;  // float4 copy of the N2 stage twiddles
+  // two-pass family: stage twiddles of length N1/2 (float2 and float4 copies)
+  // and the radix-2 twiddles W_N1^k
+  const int totm = two_pass ? gbdct::tw_size_p(n1 / 2, p->pmax) : 0;
+  const size_t tm = two_pass ? round_up(totm + 1, 2) : 0;
+  const size_t tr = two_pass ? round_up(n1 / 2 + 1, 2) : 0;
+  p->table_elems = t1 + t2 + 2 * ta + 2 * tb + tf + tx + 3 * tm + tr + 2;  // + 16 bytes for the error word
   cudaError_t e = cudaMalloc(&p->tables, p->table_elems * sizeof(float2));
   if (e != cudaSuccess) {
     free_plan(p);
@@ -434,13 +480,16 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   float2* fb = ia + ta;
   float2* ib = fb + tb;
   p->fstw = four_step ? ib + tb : nullptr;
-  float4* tw2x = four_step ? reinterpret_cast<float4*>(ib + tb + tf) : nullptr;
-  p->err = reinterpret_cast<int*>(ib + tb + tf + tx);
+  float4* tw2x = two_item_rows ? reinterpret_cast<float4*>(ib + tb + tf) : nullptr;
+  float2* twm = two_pass ? ib + tb + tf + tx : nullptr;
+  float4* tw1x = two_pass ? reinterpret_cast<float4*>(ib + tb + tf + tx + tm) : nullptr;
+  float2* r2w = two_pass ? ib + tb + tf + tx + 3 * tm : nullptr;
+  p->err = reinterpret_cast<int*>(ib + tb + tf + tx + 3 * tm + tr);
 
   p->work_bytes = (size_t)batch * (size_t)(n1 / 2) * (size_t)n2 * sizeof(float2);
   e = cudaMalloc(&p->work, p->work_bytes);
   // staging array for the map kernels of the other kinds (fs2 folds the maps in)
-  if (e == cudaSuccess && kind != GBDCT_DCT2 && p->family != FAM_FS2)
+  if (e == cudaSuccess && kind != GBDCT_DCT2 && !folds_maps(p->family))
     e = cudaMalloc(&p->tmp, (size_t)batch * (size_t)n1 * (size_t)n2 * sizeof(float));
   if (e != cudaSuccess) {
     free_plan(p);
@@ -452,7 +501,7 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   const int nt = (n1 / 2 + 1 > n2) ? (n1 / 2 + 1) : n2;
   k_gen_dct_tables<<<(nt + 255) / 256, 256>>>(fa, fb, ia, ib, n1, n2);
   int fsA = 0, fsB = 0;
-  if (p->family == FAM_FS2) {
+  if (four_step) {
     gbdct::fs2_split(p->lg1, &fsA, &fsB);
     if (split_a && n1 / split_a >= 16 && n1 / split_a <= 128) {
       fsA = split_a;
@@ -461,6 +510,13 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   }
   if (p->fstw) k_gen_fs_twiddles<<<(n1 + 255) / 256, 256>>>(p->fstw, n1, fsA, fsB);
   if (tw2x && tot2 > 0) k_expand_twiddles<<<(tot2 + 255) / 256, 256>>>(tw2, tw2x, tot2);
+  if (two_pass) {
+    if (totm > 0) {
+      k_gen_stage_twiddles<<<(totm + 255) / 256, 256>>>(twm, n1 / 2, p->pmax, totm);
+      k_expand_twiddles<<<(totm + 255) / 256, 256>>>(twm, tw1x, totm);
+    }
+    k_gen_r2_twiddles<<<(n1 / 2 + 256) / 256, 256>>>(r2w, n1);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemset(p->err, 0, 16);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
@@ -480,6 +536,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   a.tw1 = tw1;
   a.tw2 = tw2;
   a.tw2x = tw2x;
+  a.tw1x = tw1x;
+  a.r2w = r2w;
   a.fa = fa;
   a.fb = fb;
   a.ia = ia;
@@ -489,7 +547,8 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   a.step_filter = -1;
   a.fsA = fsA;
   a.fsB = fsB;
-  a.vkind = p->family == FAM_FS2 ? kind : 0;
+  a.tpNP = (two_pass && tp_np_ok) ? strip_np : 0;  // strip width of the column pass (0: default)
+  a.vkind = folds_maps(p->family) ? kind : 0;
   a.nsm = p->nsm;
   p->b_cols = gbdct::choose_seq_per_cta(n1, n2 / 2);
   p->b_rows = gbdct::choose_seq_per_cta(n2, n1 / 2);
@@ -497,6 +556,9 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   // Raise the dynamic shared-memory limit of the kernels once.
   if (p->family == FAM_FS2) {
     e = gbdct::run_fs2(p->lg1, p->lg2, false, a, 1, 0, true);
+  } else if (p->family == FAM_TP) {
+    e = gbdct::run_tp(p->lg1, p->lg2, false, a, 1, 0, true);
+    if (e == cudaSuccess) e = gbdct::run_fs2(p->lg1, p->lg2, false, a, 1, 0, true);
   } else if (p->family == FAM_PAIR) {
     e = gbdct::run_fwd_cols2(p->lg1, a, 1, 1, 0, true);
     if (e == cudaSuccess) e = gbdct::run_inv_cols2(p->lg1, a, 1, 1, 0, true);
@@ -528,7 +590,7 @@ gbdct_status gbdct_plan_create(gbdct_plan_t* out, int ndim, const int64_t* dims,
 }
 
 static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse,
-                              int step = -1);
+                              int step = -1, bool io_dev = false);
 static int core_launches(gbdct_plan_t p) {
   return p->family == FAM_FS2 ? 3 : 2;
 }
@@ -548,14 +610,16 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
   if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return GBDCT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!device_accessible(in, p->device, s) || !device_accessible(out, p->device, s)) return GBDCT_ERR_INVALID_ARG;
+  const int kin = pointer_kind(in, p->device, s), kout = pointer_kind(out, p->device, s);
+  if (kin == PTR_NONE || kout == PTR_NONE) return GBDCT_ERR_INVALID_ARG;
+  const bool io_dev = kin == PTR_DEVICE && kout == PTR_DEVICE;
   if (p->ndim == 3) return exec3d(p, in, out, s, inverse, step);
   if (p->precision == GBDCT_PREC_SPLIT_BF16)
     return step >= 0 ? GBDCT_ERR_UNSUPPORTED
                      : gbdct::gemm_exec(p->gemm, inverse, static_cast<const float*>(in), static_cast<float*>(out), s);
-  if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse, step);
+  if (p->kind == GBDCT_DCT2) return exec_core(p, in, out, s, inverse, step, io_dev);
   if (!inverse && (p->kind == GBDCT_IDCT_IDXST || p->kind == GBDCT_IDXST_IDCT)) return GBDCT_ERR_UNSUPPORTED;
-  if (p->family == FAM_FS2) return exec_core(p, in, out, s, inverse, step);  // maps folded in (vkind)
+  if (folds_maps(p->family)) return exec_core(p, in, out, s, inverse, step, io_dev);  // maps folded in (vkind)
   MapSpec pre{}, post{};
   if (p->kind == GBDCT_DST2) {
     if (!inverse) {
@@ -591,16 +655,24 @@ static gbdct_status exec2d(gbdct_plan_t p, const void* in, void* out, void* stre
 }
 
 static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStream_t s, bool inverse,
-                              int step) {
+                              int step, bool io_dev) {
   Dct2dArgs a = p->args;
   a.in = static_cast<const float*>(in);
   a.out = static_cast<float*>(out);
   a.step_filter = step;
+  a.io_dev = io_dev ? 1 : 0;
+  a.polls = p->wait_polls;
   const int batch = (int)p->batch;
   const bool s0 = step < 0 || step == 0, s1 = step < 0 || step == 1;
   cudaError_t e = cudaSuccess;
   if (p->family == FAM_FS2) {
     return cuda_status(gbdct::run_fs2(p->lg1, p->lg2, inverse, a, batch, s, false));
+  }
+  if (p->family == FAM_TP) {
+    // host-mapped or managed buffers: the four-step kernels (full transforms
+    // only; single steps keep the two-pass launch sequence)
+    if (!io_dev && step < 0) return cuda_status(gbdct::run_fs2(p->lg1, p->lg2, inverse, a, batch, s, false));
+    return cuda_status(gbdct::run_tp(p->lg1, p->lg2, inverse, a, batch, s, false));
   }
   if (p->family == FAM_PAIR) {
     if (!inverse) {
@@ -653,18 +725,23 @@ const char* gbdct_plan_step_name(gbdct_plan_t plan, int inverse, int step) {
                                 "row pass (row FFT + symmetric-pair postprocess)"};
   static const char* kInv2[] = {"row pass (four-read preprocess + row IFFT)",
                                 "column pass (column IFFT + inverse reorder)"};
+  static const char* kFwdTp[] = {"column pass (reorder + half-length column FFTs)",
+                                 "row pass (radix-2 step + split + row FFT + postprocess)"};
+  static const char* kInvTp[] = {"row pass (preprocess + row IFFT + pairing + radix-2 step)",
+                                 "column pass (half-length column IFFTs + inverse reorder)"};
   static const char* kFwd3[] = {"column step C1 (reorder + DFT_B + twiddle)", "column step C2 (DFT_A)",
                                 "row pass (split + row FFT + postprocess)"};
   static const char* kInv3[] = {"row pass (preprocess + row IFFT + pairing)", "column step C2' (DFT_A + twiddle)",
                                 "column step C1' (DFT_B + inverse reorder)"};
   const bool three = core_launches(plan) == 3;
   int k = step;
-  if (plan->kind != GBDCT_DCT2 && plan->family != FAM_FS2) {
+  if (plan->kind != GBDCT_DCT2 && !folds_maps(plan->family)) {
     if (k == 0) return "index/sign map (pre)";
     if (k == gbdct_plan_launches_per_exec(plan) - 1) return "index/sign map (post)";
     k -= 1;
   }
   if (three) return inverse ? kInv3[k] : kFwd3[k];
+  if (plan->family == FAM_TP) return inverse ? kInvTp[k] : kFwdTp[k];
   return inverse ? kInv2[k] : kFwd2[k];
 }
 
@@ -701,17 +778,22 @@ int gbdct_plan_launches_per_exec(gbdct_plan_t plan) {
   if (plan->precision == GBDCT_PREC_SPLIT_BF16) return 3;  // split kernel + two tensor-core products
   if (plan->ndim == 3) return gbdct_plan_launches_per_exec(plan->inner) + 1;
   const int core = core_launches(plan);
-  return (plan->kind == GBDCT_DCT2 || plan->family == FAM_FS2) ? core : core + 2;
+  return (plan->kind == GBDCT_DCT2 || folds_maps(plan->family)) ? core : core + 2;
 }
 
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan) {
   if (!plan) return "";
-  return plan->family == FAM_FS2 ? "fs2" : plan->family == FAM_PAIR ? "pair" : "seq";
+  switch (plan->family) {
+    case FAM_TP: return "tp";
+    case FAM_FS2: return "fs2";
+    case FAM_PAIR: return "pair";
+  }
+  return "seq";
 }
 
 gbdct_status gbdct_plan_set_threshold(gbdct_plan_t plan, float eps) {
   if (!plan || !(eps >= 0.f)) return GBDCT_ERR_INVALID_ARG;
-  if (plan->ndim != 2 || plan->family != FAM_FS2 || plan->n2 > 8192) return GBDCT_ERR_UNSUPPORTED;
+  if (plan->ndim != 2 || !folds_maps(plan->family) || plan->n2 > 8192) return GBDCT_ERR_UNSUPPORTED;
   plan->args.thresh = eps;
   return GBDCT_OK;
 }

@@ -58,19 +58,7 @@ __global__ void k_split(const float* __restrict__ v, __nv_bfloat16* __restrict__
   lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() { return tma::encoder(); }
 
 // 2D bf16 map of a row-major rows x cols matrix, box 64 (cols) x box_rows, 128-byte swizzle.
 bool map2d(CUtensorMap* m, const void* base, long long rows, long long cols, int box_rows) {

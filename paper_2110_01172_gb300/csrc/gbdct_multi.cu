@@ -46,9 +46,11 @@ gbdct_status cuda_err(cudaError_t e) {
 // Autotuner
 // ---------------------------------------------------------------------------
 
-// candidates: the kernel families, and the four-step family with each split
-// N1 = A * (N1 / A) of its column FFT (tile shape of the column steps)
-const char* const kFamilies[] = {"fs2", "pair", "seq", "fs2/16", "fs2/32", "fs2/64", "fs2/128"};
+// candidates: the kernel families, the four-step family with each split
+// N1 = A * (N1 / A) of its column FFT (tile shape of the column steps), and
+// the two-pass family with each strip width (column pairs per CTA)
+const char* const kFamilies[] = {"tp",     "fs2",    "pair",    "seq",  "fs2/16", "fs2/32", "fs2/64", "fs2/128",
+                                 "tp/1",   "tp/2",   "tp/4",    "tp/8", "tp/16",  "tp/32"};
 
 std::mutex g_tune_mu;
 std::map<std::string, std::string>* g_tune = nullptr;  // key -> family

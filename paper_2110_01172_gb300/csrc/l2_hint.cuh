@@ -9,6 +9,7 @@
 // 4096^2: the first column step wrote its whole 64 MB output to DRAM).
 // The policies are created once per thread (createpolicy) and passed to
 // ld/st.global.L2::cache_hint; the hint only changes replacement priority.
+// ld_once additionally skips L1 allocation for data that is read only once.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,6 +42,23 @@ __device__ __forceinline__ float2 ld(const float2* a, uint64_t pol) {
 __device__ __forceinline__ float4 ld(const float4* a, uint64_t pol) {
   float4 v;
   asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a), "l"(pol));
+  return v;
+}
+
+// Loads of data read exactly once: not allocated in L1, so that the streamed
+// data does not evict what the CTA reuses from L1 (twiddle tables).
+__device__ __forceinline__ float2 ld_once(const float2* a, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(v.x), "=f"(v.y)
+               : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float4 ld_once(const float4* a, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "l"(a), "l"(pol));
   return v;

@@ -1,0 +1,67 @@
+// pass_tp_rows.cu - row passes of the two-pass family (radix-2 column step
+// folded into the loads / stores), and the whole-transform launcher
+// (forward: column pass, row pass; inverse: row pass, column pass).
+#include "dct2d_launch.cuh"
+#include "dct2d_tp_kernels.cuh"
+
+namespace gbdct {
+namespace {
+
+template <int L>
+cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  using R = RowX2Geom<L>;
+  if (prepare) {
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_fwd<L>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, false>),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, true>),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    return e;
+  }
+  if ((a.n1 / 4) % R::NP) return cudaErrorInvalidValue;
+  const dim3 grid(a.n1 / 4 / R::NP, 1, batch);
+  if (inverse && (a.vkind == 1 || a.vkind == 2))
+    k_tp_rows_inv<L, true><<<grid, R::THREADS, R::SMEM, s>>>(a);
+  else if (inverse)
+    k_tp_rows_inv<L, false><<<grid, R::THREADS, R::SMEM, s>>>(a);
+  else
+    k_tp_rows_fwd<L><<<grid, R::THREADS, R::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t run_rows(int lg2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  switch (lg2) {
+    case 8: return row_launch<256>(inverse, a, batch, s, prepare);
+    case 9: return row_launch<512>(inverse, a, batch, s, prepare);
+    case 10: return row_launch<1024>(inverse, a, batch, s, prepare);
+    case 11: return row_launch<2048>(inverse, a, batch, s, prepare);
+    case 12: return row_launch<4096>(inverse, a, batch, s, prepare);
+    case 13: return row_launch<8192>(inverse, a, batch, s, prepare);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t run_tp(int lg1, int lg2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  if (prepare) {
+    cudaError_t e = run_rows(lg2, false, a, batch, s, true);
+    if (e == cudaSuccess) e = run_tp_cols(lg1, false, a, batch, s, true);
+    return e;
+  }
+  const int f = a.step_filter;
+  cudaError_t e = cudaSuccess;
+  if (!inverse) {
+    if (f < 0 || f == 0) e = run_tp_cols(lg1, false, a, batch, s, false);
+    if (e == cudaSuccess && (f < 0 || f == 1)) e = run_rows(lg2, false, a, batch, s, false);
+  } else {
+    if (f < 0 || f == 0) e = run_rows(lg2, true, a, batch, s, false);
+    if (e == cudaSuccess && (f < 0 || f == 1)) e = run_tp_cols(lg1, true, a, batch, s, false);
+  }
+  return e;
+}
+
+}  // namespace gbdct

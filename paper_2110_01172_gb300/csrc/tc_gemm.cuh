@@ -31,12 +31,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tma_util.cuh"
+
 namespace gbdct {
 namespace tc {
 
 constexpr int BM = 128;                  // tile rows (MMA M)
 constexpr int BK = 64;                   // K per stage: one 128-byte swizzle row of bf16
-constexpr uint32_t kDefaultPolls = 1u << 21;
+constexpr uint32_t kDefaultPolls = tma::kDefaultPolls;
+using tma::bar_wait;
+using tma::su32;
 enum { EPI_SPLIT_T = 0, EPI_F32 = 1 };
 
 template <int BN>
@@ -60,23 +64,6 @@ struct Epi {
   __nv_bfloat16* tl;
   float* out;               // EPI_F32 output
 };
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, uint32_t polls) {
-  for (uint32_t it = 0; it < polls; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (it >= 16) __nanosleep(256);
-  }
-  return false;
-}
 
 // Shared-memory matrix descriptor of a K-major bf16 tile with the 128-byte
 // swizzle: 8-row groups of 128-byte rows, 1024 bytes apart.

@@ -132,7 +132,7 @@ def test_tuned_multi_and_forced_families():
     xs = _inputs(shapes, 400)
     m = MultiPlan(shapes, tuned=True)
     fams = m.group_families()
-    assert len(fams) == 3 and all(f in ("seq", "pair", "fs2") or f.startswith("fs2/") for f in fams)
+    assert len(fams) == 3 and all(f in ("seq", "pair", "fs2", "tp") or f.startswith(("fs2/", "tp/")) for f in fams)
     X = m.forward(m.pack([torch.from_numpy(x) for x in xs]))
     torch.cuda.synchronize()
     for x, Xi in zip(xs, m.unpack(X)):
@@ -149,6 +149,9 @@ def test_tuned_multi_and_forced_families():
         assert rel <= REL_L2 and mx <= MAX_ABS
     with pytest.raises(GbdctError):
         Plan((128, 512), family="fs2")    # fs2 needs N1 >= 256
+    with pytest.raises(GbdctError):
+        Plan((256, 512), family="tp")     # tp needs N1 >= 512
+    assert Plan((512, 256), family="tp").family == "tp"
     assert Plan((64, 64, 64), family="seq").family == "seq"
 
 

@@ -180,10 +180,11 @@ FAMILY_SUPPORT = {
     "seq": lambda s: True,
     "pair": lambda s: all(16 <= n <= 8192 for n in s),
     "fs2": lambda s: 256 <= s[0] <= 8192 and 256 <= s[1] <= 16384,
+    "tp": lambda s: 512 <= s[0] <= 8192 and 256 <= s[1] <= 8192,
 }
 
 
-@pytest.mark.parametrize("family", ["seq", "pair", "fs2"])
+@pytest.mark.parametrize("family", ["seq", "pair", "fs2", "tp"])
 @pytest.mark.parametrize("shape", [(4096, 4096), (2048, 4096), (1024, 8192), (4096, 8192), (1024, 4096),
                                    (8192, 2048)])
 def test_every_kernel_family_matches_oracle(family, shape, monkeypatch):
@@ -213,6 +214,31 @@ def test_every_four_step_split_matches_oracle(shape, a):
     plan.close()
 
 
+@pytest.mark.parametrize("shape,np_", [((4096, 4096), 2), ((4096, 4096), 4), ((2048, 2048), 2), ((2048, 2048), 8),
+                                       ((8192, 1024), 1), ((8192, 1024), 2), ((512, 4096), 8), ((512, 256), 32),
+                                       ((1024, 512), 16)])
+def test_every_two_pass_strip_width_matches_oracle(shape, np_):
+    """The autotuner's tile candidates of the two-pass family: column strips of
+    NP column pairs (NP * 16 bytes of every row), against the full oracle."""
+    from paper_2110_01172_gb300 import Plan
+    plan = Plan(shape, "dct2", family=f"tp/{np_}")
+    assert plan.family == "tp"
+    _check_full(plan, shape, seed=19)
+    plan.close()
+
+
+def test_invalid_two_pass_strip_widths_are_rejected():
+    from paper_2110_01172_gb300 import GbdctError, Plan
+    with pytest.raises(GbdctError):
+        Plan((4096, 4096), family="tp/8")      # 1024 threads per CTA
+    with pytest.raises(GbdctError):
+        Plan((512, 4096), family="tp/1")       # 16 threads per CTA
+    with pytest.raises(GbdctError):
+        Plan((1024, 1024), family="tp/3")      # not a power of two
+    with pytest.raises(GbdctError):
+        Plan((256, 1024), family="tp/16")      # N1 below the family's range
+
+
 def test_invalid_four_step_splits_are_rejected():
     from paper_2110_01172_gb300 import GbdctError, Plan
     with pytest.raises(GbdctError):
@@ -223,7 +249,7 @@ def test_invalid_four_step_splits_are_rejected():
         Plan((1024, 1024), family="fs2/48")    # not a supported factor
 
 
-@pytest.mark.parametrize("family", ["fs2"])
+@pytest.mark.parametrize("family", ["fs2", "tp"])
 def test_batched_four_step_families(family, monkeypatch):
     monkeypatch.setenv("GBDCT_KERNEL_FAMILY", family)
     from paper_2110_01172_gb300 import Plan, binding
@@ -243,9 +269,9 @@ def test_batched_four_step_families(family, monkeypatch):
     assert plan.check_device_error() == binding.OK
 
 
-@pytest.mark.parametrize("family", ["seq", "pair", "fs2"])
+@pytest.mark.parametrize("family", ["seq", "pair", "fs2", "tp"])
 @pytest.mark.parametrize("shape", [(256, 512), (64, 2048), (256, 256), (512, 256), (2048, 256), (256, 16384),
-                                   (8192, 256)])
+                                   (8192, 256), (512, 8192), (8192, 512)])
 def test_small_families_full_oracle(family, shape, monkeypatch):
     if not FAMILY_SUPPORT[family](shape):
         pytest.skip(f"{family} does not support {shape}")
@@ -261,7 +287,7 @@ def test_small_families_full_oracle(family, shape, monkeypatch):
     check(y.cpu().numpy(), oracle.idct2_2d(X.cpu().numpy()))
 
 
-@pytest.mark.parametrize("family", ["pair", "seq", "fs2"])
+@pytest.mark.parametrize("family", ["pair", "seq", "fs2", "tp"])
 def test_single_steps_compose_to_the_full_transform(family, monkeypatch):
     """gbdct_exec_step run for every launch in order equals the full call."""
     shape = (1024, 4096)
@@ -285,8 +311,9 @@ def test_single_steps_compose_to_the_full_transform(family, monkeypatch):
     assert torch.equal(back, plan.inverse(full))
 
 
-@pytest.mark.parametrize("shape", [(256, 512), (1024, 1024), (2048, 4096)])
-def test_compression_threshold_fused_in_forward(shape):
+@pytest.mark.parametrize("shape,family", [((256, 512), "fs2"), ((1024, 1024), "fs2"), ((2048, 4096), "fs2"),
+                                          ((512, 256), "tp"), ((4096, 4096), "tp")])
+def test_compression_threshold_fused_in_forward(shape, family):
     """Section V-A, Eq. image-compression / Algorithm 3: the forward output with
     |X| < eps stored as zero by the forward's last stores.  The GPU decision
     is taken in FP32 on the same values as the unthresholded forward, so the
@@ -296,7 +323,7 @@ def test_compression_threshold_fused_in_forward(shape):
     from paper_2110_01172_gb300 import Plan
     x = inputs.gaussian_bumps(shape, seed=11)
     xd = torch.from_numpy(x).cuda()
-    plan = Plan(shape)
+    plan = Plan(shape, family=family)
     X = plan.forward(xd).cpu().numpy()
     ref = oracle.dct2_2d(x)
     eps = np.float32(1e-3 * np.abs(ref).max())
@@ -320,6 +347,27 @@ def test_compression_threshold_fused_in_forward(shape):
 def test_compression_threshold_rejections():
     from paper_2110_01172_gb300 import GbdctError, Plan
     with pytest.raises(GbdctError):
-        Plan((128, 128)).set_threshold(0.5)        # not a four-step plan
+        Plan((128, 128)).set_threshold(0.5)        # neither a four-step nor a two-pass plan
     with pytest.raises(GbdctError):
         Plan((256, 256)).set_threshold(-1.0)       # negative threshold
+
+
+def test_two_pass_bulk_copy_wait_timeout_is_reported_and_recovers():
+    """The two-pass column pass waits (bounded) for its bulk tensor copies; a
+    bound of one poll makes the waits give up: the failure is recorded in the
+    plan's device error word (the strips are left unwritten, the copies are
+    still waited for), and with the default bound the transform is exact again."""
+    from paper_2110_01172_gb300 import Plan, binding
+    shape = (2048, 2048)
+    plan = Plan(shape, family="tp")
+    x, X, Y, y_ref = _oracle_pair(shape, 23)
+    xd = torch.from_numpy(x).cuda()
+    assert plan.check_device_error() == binding.OK
+    plan.set_wait_limit(1)
+    plan.forward(xd)
+    torch.cuda.synchronize()
+    assert plan.check_device_error() == binding.ERR_TIMEOUT
+    assert plan.check_device_error() == binding.OK      # reported once, then cleared
+    plan.set_wait_limit(0)
+    _check_full(plan, shape, seed=23)
+    assert plan.check_device_error() == binding.OK

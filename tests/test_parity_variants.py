@@ -65,23 +65,26 @@ def test_idxst_kinds(kind, shape):
     assert plan.forward_ptr(buf.data_ptr(), buf.data_ptr()) == binding.ERR_UNSUPPORTED
 
 
-FOLD_SHAPES = [(256, 256), (512, 256), (256, 1024), (1024, 512), (256, 16384)]
+FOLD_SHAPES = [(256, 256), (512, 256), (256, 1024), (1024, 512), (256, 16384), (2048, 512), (512, 2048)]
+LAUNCHES = {"fs2": 3, "tp": 2, "pair": 4}
 
 
-@pytest.mark.parametrize("family", ["fs2", "pair"])
+@pytest.mark.parametrize("family", ["fs2", "tp", "pair"])
 @pytest.mark.parametrize("shape", FOLD_SHAPES)
 def test_kinds_folded_and_mapped_paths(family, shape):
-    """fs2 folds each kind's index/sign maps into its first loads and last
-    stores; pair runs the map kernels around the DCT-II.  Both against the
+    """fs2 and tp fold each kind's index/sign maps into their first loads and
+    last stores; pair runs the map kernels around the DCT-II.  All against the
     oracle, for every kind, forward and inverse where defined."""
     from paper_2110_01172_gb300 import Plan
     if family == "pair" and max(shape) > 8192:
         pytest.skip("pair supports sides up to 8192")
+    if family == "tp" and not (shape[0] >= 512 and shape[1] <= 8192):
+        pytest.skip("tp supports N1 >= 512, N2 <= 8192")
     x = inputs.uniform(shape, seed=44)
     xd = torch.from_numpy(x).cuda()
     p = Plan(shape, "dst2", family=family)
     assert p.family == family
-    assert p.launches_per_exec == (3 if family == "fs2" else 4)
+    assert p.launches_per_exec == LAUNCHES[family]
     S = p.forward(xd)
     back = p.inverse(S)
     torch.cuda.synchronize()
@@ -100,7 +103,7 @@ def test_folded_kinds_batched_and_in_place():
     shape = (512, 1024)
     xs = np.stack([inputs.uniform(shape, seed=45 + i) for i in range(3)])
     p = Plan(shape, "dst2", batch=3)
-    assert p.family == "fs2"
+    assert p.family == "tp"            # the default family folds the maps in
     xd = torch.from_numpy(xs).cuda()
     S = p.forward(xd)
     torch.cuda.synchronize()
