@@ -29,6 +29,7 @@
 #pragma once
 
 #include "dct2d_fs2_kernels.cuh"
+#include "launch_dep.cuh"
 #include "tma_util.cuh"
 
 namespace gbdct {
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(TpColGeom<M, NP>::THREADS, TpColGeom<M, NP>::M
               vcol;
   float4* s = stc + pi;
   const uint64_t pol_stream = l2::evict_first();
+  pdl::wait_prior_grid();
   soa::C2 v[16];
   if constexpr (!INV) {
     const float4* xin = reinterpret_cast<const float4*>(a.in + (long long)blockIdx.z * a.in_bstride) + vcol;
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(TpColGeom<M, NP>::THREADS, TpColGeom<M, NP>::M
   soa::first_stage<M, INV, G::NP>(v, s, g);
   __syncthreads();
   soa::stages<M, 16, INV, G::NP>(s, g, a.tw1x);
+  pdl::launch_dependents();
   if constexpr (!INV) {
     const uint64_t pol_keep = l2::evict_last();  // read again by the row pass
 #pragma unroll 4
@@ -163,6 +166,9 @@ __global__ void __launch_bounds__(TpColGeom<M, NP>::THREADS, TpColGeom<M, NP>::M
   if (threadIdx.x == 0) {
     tma::bar_init(bar, 1);
     tma::fence_barrier_init();
+  }
+  pdl::wait_prior_grid();
+  if (threadIdx.x == 0) {
     tma::bar_expect_tx(bar, (uint32_t)(M * NP * sizeof(float4)));
     const uint64_t pol = l2::evict_first();  // input streamed once / last use of the workspace
     if constexpr (!INV) {
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(TpColGeom<M, NP>::THREADS, TpColGeom<M, NP>::M
       for (int z = 0; z < M; z += ZB) tma::load_3d(buf + z * NP, &mw, x0, par * M + z, b, bar, pol);
     }
     const uint32_t polls = a.polls ? a.polls : tma::kDefaultPolls;
-    int ok = tma::bar_wait(bar, 0, polls);
+    int ok = tma::bar_wait_from_issue(bar, 0, polls);
     if (!ok) {
       atomicExch(a.err, 1);
       tma::bar_wait(bar, 0, tma::kDefaultPolls);  // the copies must land before the CTA exits
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(TpColGeom<M, NP>::THREADS, TpColGeom<M, NP>::M
   if (!*flag) return;
   // every thread observes the completed phase (acquire of the copied data);
   // it has completed, so the first, non-blocking poll succeeds
-  if (threadIdx.x) tma::bar_wait(bar, 0, 1);
+  if (threadIdx.x) tma::test_wait(bar, 0);
   soa::C2 v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
@@ -219,6 +225,7 @@ __global__ void __launch_bounds__(TpColGeom<M, NP>::THREADS, TpColGeom<M, NP>::M
   }
   tma::fence_proxy_async();
   __syncthreads();
+  pdl::launch_dependents();
   if (threadIdx.x == 0) {
     if constexpr (!INV) {
       const uint64_t pol = l2::evict_last();  // read again by the row pass
@@ -265,6 +272,7 @@ __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB) k_t
   const float2 w2 = first ? __ldg(a.r2w + M / 2) : conjf2(w);
   const int t = mirror_lane_butterfly<TPS>(g);
   const uint64_t pol = l2::evict_first();  // last use of the workspace
+  pdl::wait_prior_grid();
   soa::C2 v[16];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -280,6 +288,7 @@ __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB) k_t
   soa::first_stage<L, false>(v, s, t);
   __syncthreads();
   soa::stages<L, 16, false>(s, g, a.tw2x);
+  pdl::launch_dependents();
   fwd_post_x2<L>(s, a, a.out + (long long)blockIdx.z * a.out_bstride, c, kb, first, g);
 }
 
@@ -333,6 +342,7 @@ __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB_INV)
   const int kb = tp_item_b(c, M);
   const float* C = a.in + (long long)blockIdx.z * a.in_bstride;
   const InvRows A = inv_rows_of(a, C, c, L), B = inv_rows_of(a, C, kb, L);
+  pdl::wait_prior_grid();
   soa::C2 v[16];
   if (first)
     inv_pre_x2<L, MAPPED, true>(a, A, B, c, kb, g, v);
@@ -341,6 +351,7 @@ __global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB_INV)
   soa::first_stage<L, true>(v, s, g);
   __syncthreads();
   soa::stages<L, 16, true>(s, g, a.tw2x);
+  pdl::launch_dependents();
   tp_inv_pair<L>(s, a, a.work + (long long)blockIdx.z * a.work_bstride, c, kb, first, g);
 }
 

@@ -56,16 +56,14 @@ cudaError_t col_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t
     CUtensorMap mx, mw;
     if (a.io_dev && encode_maps(a, batch, inverse, NP, G::ZB, &mx, &mw)) {
       if (inverse)
-        k_tp_cols_tma<M, NP, true><<<grid, G::THREADS, G::SMEM_TMA, s>>>(a, mx, mw);
+        return pdl::launch(k_tp_cols_tma<M, NP, true>, grid, dim3(G::THREADS), G::SMEM_TMA, s, a, mx, mw);
       else
-        k_tp_cols_tma<M, NP, false><<<grid, G::THREADS, G::SMEM_TMA, s>>>(a, mx, mw);
-      return cudaGetLastError();
+        return pdl::launch(k_tp_cols_tma<M, NP, false>, grid, dim3(G::THREADS), G::SMEM_TMA, s, a, mx, mw);
     }
     if (inverse)
-      k_tp_cols<M, NP, true><<<grid, G::THREADS, G::SMEM, s>>>(a);
+      return pdl::launch(k_tp_cols<M, NP, true>, grid, dim3(G::THREADS), G::SMEM, s, a);
     else
-      k_tp_cols<M, NP, false><<<grid, G::THREADS, G::SMEM, s>>>(a);
-    return cudaGetLastError();
+      return pdl::launch(k_tp_cols<M, NP, false>, grid, dim3(G::THREADS), G::SMEM, s, a);
   }
 }
 

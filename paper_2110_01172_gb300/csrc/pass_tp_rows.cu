@@ -24,12 +24,11 @@ cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t
   if ((a.n1 / 4) % R::NP) return cudaErrorInvalidValue;
   const dim3 grid(a.n1 / 4 / R::NP, 1, batch);
   if (inverse && (a.vkind == 1 || a.vkind == 2))
-    k_tp_rows_inv<L, true><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    return pdl::launch(k_tp_rows_inv<L, true>, grid, dim3(R::THREADS), R::SMEM, s, a);
   else if (inverse)
-    k_tp_rows_inv<L, false><<<grid, R::THREADS, R::SMEM, s>>>(a);
+    return pdl::launch(k_tp_rows_inv<L, false>, grid, dim3(R::THREADS), R::SMEM, s, a);
   else
-    k_tp_rows_fwd<L><<<grid, R::THREADS, R::SMEM, s>>>(a);
-  return cudaGetLastError();
+    return pdl::launch(k_tp_rows_fwd<L>, grid, dim3(R::THREADS), R::SMEM, s, a);
 }
 
 cudaError_t run_rows(int lg2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {

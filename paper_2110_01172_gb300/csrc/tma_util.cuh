@@ -33,31 +33,43 @@ __device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
 }
 
-// Waits for phase `parity` of the barrier to complete, at most `polls` polls.
-// The first poll does not block (test_wait), so a bound of one poll gives up
-// on any copy still in flight; later polls may suspend briefly (try_wait).
+__device__ __forceinline__ bool test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier to complete, at most `polls` polls
+// (try_wait: a poll may suspend the thread briefly).
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, uint32_t polls) {
   for (uint32_t it = 0; it < polls; ++it) {
-    uint32_t ok;
-    if (it == 0) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(ok)
-          : "r"(su32(bar)), "r"(parity)
-          : "memory");
-    } else {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(ok)
-          : "r"(su32(bar)), "r"(parity)
-          : "memory");
-    }
-    if (ok) return true;
+    if (try_wait(bar, parity)) return true;
     if (it >= 16) __nanosleep(256);
   }
   return false;
+}
+
+// As bar_wait, but the first poll does not block (test_wait), so a bound of
+// one poll gives up on any copy still in flight right after it was issued.
+__device__ __forceinline__ bool bar_wait_from_issue(uint64_t* bar, uint32_t parity, uint32_t polls) {
+  if (polls == 0) return false;
+  if (test_wait(bar, parity)) return true;
+  return bar_wait(bar, parity, polls - 1);
 }
 
 // Tiled tensor loads into shared memory, completing on `bar` (transaction
