@@ -157,10 +157,10 @@ int gbdct_plan_launches_per_exec(gbdct_plan_t plan);
 
 /* Name of the kernel family the plan runs ("seq", "pair", "fs2" or "tp"; ""
  * for a NULL plan).  Every family computes the same transform; the plan picks
- * the fastest one that supports the shape (tp: N1 in 512..8192 and N2 in
- * 256..8192, two launches per direction; fs2: N1 in 256..8192 and N2 in
- * 256..16384, three launches; pair: both sides in 16..8192; seq: any
- * supported size), and the environment variable
+ * the fastest one that supports the shape (tp: both sides in 128..8192, two
+ * launches per direction, the default for N1 <= 4096; fs2: N1 in 256..8192
+ * and N2 in 256..16384, three launches; pair: both sides in 16..8192; seq:
+ * any supported size), and the environment variable
  * GBDCT_KERNEL_FAMILY=seq|pair|fs2|tp, read at plan creation, forces a family
  * when it supports the shape (for testing and comparison). */
 const char* gbdct_plan_kernel_family(gbdct_plan_t plan);

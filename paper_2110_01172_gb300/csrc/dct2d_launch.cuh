@@ -57,13 +57,13 @@ inline void fs2_split(int log2N1, int* A, int* B) {
   *B = n1 / *A;
 }
 
-// Two-pass family: N1 in {512, ..., 8192}, N2 in {256, ..., 8192}.  One call
+// Two-pass family: N1 in {128, ..., 8192}, N2 in {128, ..., 8192}.  One call
 // launches the whole forward (column pass, row pass) or inverse (row pass,
 // column pass).
 cudaError_t run_tp(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s,
                    bool prepare);
 cudaError_t run_tp_cols(int lg1, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare);
-constexpr int kTpMinLog2N1 = 9, kTpMaxLog2N1 = 13, kTpMinLog2N2 = 8, kTpMaxLog2N2 = 13;
+constexpr int kTpMinLog2N1 = 7, kTpMaxLog2N1 = 13, kTpMinLog2N2 = 7, kTpMaxLog2N2 = 13;
 // Strip widths NP (column pairs per CTA) the two-pass column pass is built
 // for at half-length M: 128 to 512 threads (M/16 per pair), the strip's
 // padded shared memory within 227 KB, and N2/4 float4 columns a multiple of NP.

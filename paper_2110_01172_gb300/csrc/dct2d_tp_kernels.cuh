@@ -25,7 +25,7 @@
 // Eq. (2d_idct_post).
 //
 // Workspace: N1 rows of N2/2 complex; rows [0, M) hold E (E'), rows [M, N1) O (O').
-// Supported: N1 in {512, ..., 8192}, N2 in {256, ..., 8192}.
+// Supported: N1 in {128, ..., 8192}, N2 in {128, ..., 8192}.
 #pragma once
 
 #include "dct2d_fs2_kernels.cuh"

@@ -3,6 +3,7 @@
 
 #include "dct2d_kernels.cuh"
 #include "fft_core.cuh"
+#include "launch_dep.cuh"
 
 namespace gbdct {
 namespace {
@@ -39,6 +40,7 @@ __global__ void __launch_bounds__(512, 2) k_axis0(AxisArgs a) {
   // rows rg, rg + TPS, ...: a strided pointer, eight loads in flight per thread
   const float* src = X + (long long)rg * a.M + col;
   const long long rstep = (long long)G::TPS * a.M;
+  pdl::wait_prior_grid();  // the slices' last launch wrote (or reads) this array
   if constexpr (!INV) {
 #pragma unroll 8
     for (int j = 0; j < G::PTS; ++j) {
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(512, 2) k_axis0(AxisArgs a) {
     }
     __syncthreads();
     fft_stages<N, 1, false>(sm + (t / G::TPS) * G::SP, t % G::TPS, a.tw);
+    pdl::launch_dependents();
 #pragma unroll
     for (int j = 0; j < G::PTS; ++j) {
       const int k = rg + j * G::TPS;
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(512, 2) k_axis0(AxisArgs a) {
     }
     __syncthreads();
     fft_stages<N, 1, true>(sm + (t / G::TPS) * G::SP, t % G::TPS, a.tw);
+    pdl::launch_dependents();
 #pragma unroll
     for (int j = 0; j < G::PTS; ++j) {
       const int n = rg + j * G::TPS;
@@ -105,11 +109,8 @@ cudaError_t launch(bool inverse, const AxisArgs& a, int batch, cudaStream_t s, b
   const long long ctas = a.M / (2LL * P);
   if (ctas < 1 || ctas > 0x7fffffffLL || batch < 1 || batch > 65535) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)ctas, (unsigned)batch);
-  if (inverse)
-    k_axis0<N, true><<<grid, P * G::TPS, smem, s>>>(a);
-  else
-    k_axis0<N, false><<<grid, P * G::TPS, smem, s>>>(a);
-  return cudaGetLastError();
+  if (inverse) return pdl::launch(k_axis0<N, true>, grid, dim3(P * G::TPS), smem, s, a);
+  return pdl::launch(k_axis0<N, false>, grid, dim3(P * G::TPS), smem, s, a);
 }
 
 }  // namespace

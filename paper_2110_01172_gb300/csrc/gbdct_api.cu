@@ -29,6 +29,7 @@ struct gbdct_plan_s {
   int family;          // kernel family (FAM_*)
   float2* fstw;        // four-step twiddles W_N1^{n1a k1b} (FAM_FS2)
   int* err;            // device error word (bounded waits that gave up)
+  bool host_fs2;       // two-pass plan that runs full transforms on host-mapped buffers with the four-step kernels
   int nsm;             // multiprocessors of the plan's device
   float* tmp;          // variant kinds: staging array (batch * N1 * N2 floats)
   int pmax;            // points per thread of the stage structure (twiddle layout)
@@ -424,9 +425,10 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   const bool tp_np_ok = tp && strip_np > 0 && gbdct::tp_strip_ok(n1 / 2, n2, strip_np);
   // Default: the two-pass family for N1 <= 4096, the four-step family where
   // it applies, else the two-sequence family, else one sequence per thread
-  // group (fastest measured at every shape they share; at N1 = 8192 the
-  // four-step column steps beat the two-pass column pass's 16 KB-per-pair
-  // strips).
+  // group (fastest measured at every shape they share: e.g. 128^2 11.9 vs
+  // 15.8 us (pair), 256^2 11.8 vs 16.5 (fs2), 4096^2 69.5 vs 76.3; at
+  // N1 = 8192 the four-step column steps beat the two-pass column pass, whose
+  // strips there are 32 bytes of 4096 rows).
   p->family = (tp && p->lg1 <= 12) ? FAM_TP : fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
   // GBDCT_KERNEL_FAMILY=seq|pair|fs2 forces a family when it supports the shape
   // (used to test and compare every kernel family on the same inputs).
@@ -449,8 +451,10 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   // a two-pass plan also carries the four-step configuration: full transforms
   // on host-mapped buffers run the four-step kernels, whose first and last
   // launches read and write whole 1 KB row segments (the two-pass column
-  // pass's 32-byte row pieces cross the host link poorly)
-  const bool four_step = p->family == FAM_FS2 || two_pass;
+  // pass's 32-byte row pieces cross the host link poorly), where the
+  // four-step family supports the shape
+  p->host_fs2 = two_pass && fs2;
+  const bool four_step = p->family == FAM_FS2 || p->host_fs2;
   const bool two_item_rows = four_step || two_pass;  // row passes on the SoA engine (float4 twiddles)
   p->pmax = 16;
 
@@ -558,7 +562,7 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
     e = gbdct::run_fs2(p->lg1, p->lg2, false, a, 1, 0, true);
   } else if (p->family == FAM_TP) {
     e = gbdct::run_tp(p->lg1, p->lg2, false, a, 1, 0, true);
-    if (e == cudaSuccess) e = gbdct::run_fs2(p->lg1, p->lg2, false, a, 1, 0, true);
+    if (e == cudaSuccess && p->host_fs2) e = gbdct::run_fs2(p->lg1, p->lg2, false, a, 1, 0, true);
   } else if (p->family == FAM_PAIR) {
     e = gbdct::run_fwd_cols2(p->lg1, a, 1, 1, 0, true);
     if (e == cudaSuccess) e = gbdct::run_inv_cols2(p->lg1, a, 1, 1, 0, true);
@@ -671,7 +675,8 @@ static gbdct_status exec_core(gbdct_plan_t p, const void* in, void* out, cudaStr
   if (p->family == FAM_TP) {
     // host-mapped or managed buffers: the four-step kernels (full transforms
     // only; single steps keep the two-pass launch sequence)
-    if (!io_dev && step < 0) return cuda_status(gbdct::run_fs2(p->lg1, p->lg2, inverse, a, batch, s, false));
+    if (!io_dev && step < 0 && p->host_fs2)
+      return cuda_status(gbdct::run_fs2(p->lg1, p->lg2, inverse, a, batch, s, false));
     return cuda_status(gbdct::run_tp(p->lg1, p->lg2, inverse, a, batch, s, false));
   }
   if (p->family == FAM_PAIR) {

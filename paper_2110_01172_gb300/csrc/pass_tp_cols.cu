@@ -85,6 +85,8 @@ cudaError_t col_np(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, 
 // a.tpNP: the strip width NP in column pairs (0: the default for M).
 cudaError_t run_tp_cols(int lg1, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
   switch (lg1) {  // M = N1 / 2
+    case 7: return col_np<64>(inverse, a, batch, s, prepare);
+    case 8: return col_np<128>(inverse, a, batch, s, prepare);
     case 9: return col_np<256>(inverse, a, batch, s, prepare);
     case 10: return col_np<512>(inverse, a, batch, s, prepare);
     case 11: return col_np<1024>(inverse, a, batch, s, prepare);

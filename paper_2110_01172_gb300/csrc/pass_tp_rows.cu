@@ -33,6 +33,7 @@ cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t
 
 cudaError_t run_rows(int lg2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
   switch (lg2) {
+    case 7: return row_launch<128>(inverse, a, batch, s, prepare);
     case 8: return row_launch<256>(inverse, a, batch, s, prepare);
     case 9: return row_launch<512>(inverse, a, batch, s, prepare);
     case 10: return row_launch<1024>(inverse, a, batch, s, prepare);

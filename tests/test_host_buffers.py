@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("shape,family", [((4096, 4096), "fs2"), ((256, 1024), None), ((64, 64), None)])
+@pytest.mark.parametrize("shape,family", [((4096, 4096), "fs2"), ((256, 1024), "pair"), ((64, 64), None)])
 def test_pinned_host_input_and_output_match_device_buffers(shape, family):
     from paper_2110_01172_gb300 import Plan
     plan = Plan(shape, family=family)

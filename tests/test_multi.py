@@ -150,7 +150,7 @@ def test_tuned_multi_and_forced_families():
     with pytest.raises(GbdctError):
         Plan((128, 512), family="fs2")    # fs2 needs N1 >= 256
     with pytest.raises(GbdctError):
-        Plan((256, 512), family="tp")     # tp needs N1 >= 512
+        Plan((64, 512), family="tp")      # tp needs N1 >= 128
     assert Plan((512, 256), family="tp").family == "tp"
     assert Plan((64, 64, 64), family="seq").family == "seq"
 

@@ -180,7 +180,7 @@ FAMILY_SUPPORT = {
     "seq": lambda s: True,
     "pair": lambda s: all(16 <= n <= 8192 for n in s),
     "fs2": lambda s: 256 <= s[0] <= 8192 and 256 <= s[1] <= 16384,
-    "tp": lambda s: 512 <= s[0] <= 8192 and 256 <= s[1] <= 8192,
+    "tp": lambda s: 128 <= s[0] <= 8192 and 128 <= s[1] <= 8192,
 }
 
 
@@ -216,7 +216,7 @@ def test_every_four_step_split_matches_oracle(shape, a):
 
 @pytest.mark.parametrize("shape,np_", [((4096, 4096), 2), ((4096, 4096), 4), ((2048, 2048), 2), ((2048, 2048), 8),
                                        ((8192, 1024), 1), ((8192, 1024), 2), ((512, 4096), 8), ((512, 256), 32),
-                                       ((1024, 512), 16)])
+                                       ((1024, 512), 16), ((256, 512), 16), ((256, 512), 32), ((128, 128), 32)])
 def test_every_two_pass_strip_width_matches_oracle(shape, np_):
     """The autotuner's tile candidates of the two-pass family: column strips of
     NP column pairs (NP * 16 bytes of every row), against the full oracle."""
@@ -236,7 +236,7 @@ def test_invalid_two_pass_strip_widths_are_rejected():
     with pytest.raises(GbdctError):
         Plan((1024, 1024), family="tp/3")      # not a power of two
     with pytest.raises(GbdctError):
-        Plan((256, 1024), family="tp/16")      # N1 below the family's range
+        Plan((64, 1024), family="tp/16")       # N1 below the family's range
 
 
 def test_invalid_four_step_splits_are_rejected():
@@ -271,7 +271,8 @@ def test_batched_four_step_families(family, monkeypatch):
 
 @pytest.mark.parametrize("family", ["seq", "pair", "fs2", "tp"])
 @pytest.mark.parametrize("shape", [(256, 512), (64, 2048), (256, 256), (512, 256), (2048, 256), (256, 16384),
-                                   (8192, 256), (512, 8192), (8192, 512)])
+                                   (8192, 256), (512, 8192), (8192, 512), (128, 128), (128, 8192), (8192, 128),
+                                   (128, 256)])
 def test_small_families_full_oracle(family, shape, monkeypatch):
     if not FAMILY_SUPPORT[family](shape):
         pytest.skip(f"{family} does not support {shape}")
@@ -347,7 +348,7 @@ def test_compression_threshold_fused_in_forward(shape, family):
 def test_compression_threshold_rejections():
     from paper_2110_01172_gb300 import GbdctError, Plan
     with pytest.raises(GbdctError):
-        Plan((128, 128)).set_threshold(0.5)        # neither a four-step nor a two-pass plan
+        Plan((64, 64)).set_threshold(0.5)          # neither a four-step nor a two-pass plan
     with pytest.raises(GbdctError):
         Plan((256, 256)).set_threshold(-1.0)       # negative threshold
 

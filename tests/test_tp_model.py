@@ -15,7 +15,7 @@ the column pass's strips tile the rows.
 import numpy as np
 import pytest
 
-SIZES = [512, 1024, 2048, 4096, 8192]
+SIZES = [128, 256, 512, 1024, 2048, 4096, 8192]
 
 
 def reorder_src(n, length):
@@ -112,14 +112,14 @@ def strip_ok(m, n2, np_):
 
 
 @pytest.mark.parametrize("n1", SIZES)
-@pytest.mark.parametrize("n2", [256, 512, 1024, 2048, 4096, 8192])
+@pytest.mark.parametrize("n2", [128, 256, 512, 1024, 2048, 4096, 8192])
 def test_default_strip_width_is_valid(n1, n2):
     m = n1 // 2
     assert strip_ok(m, n2, max(2, 128 // fft_tps(m)))     # tp_default_np: 128 threads, >= 2 pairs
 
 
 @pytest.mark.parametrize("n1", SIZES)
-@pytest.mark.parametrize("n2", [256, 512, 1024, 2048, 4096, 8192])
+@pytest.mark.parametrize("n2", [128, 256, 512, 1024, 2048, 4096, 8192])
 @pytest.mark.parametrize("np_", [1, 2, 4, 8, 16, 32])
 def test_column_pass_geometry(n1, n2, np_):
     """Column pass: NP column pairs (float4) per CTA, TPS = M/16 threads per
