@@ -844,29 +844,40 @@ __device__ __forceinline__ InvRows inv_rows_of(const Dct2dArgs& a, const float* 
   return r;
 }
 
+// One input value: from global memory with the L2 policy, or (STAGED) from a
+// copy of the row already in shared memory.
+template <bool STAGED>
+__device__ __forceinline__ float inv_ld(const float* p, uint64_t pol) {
+  if constexpr (STAGED) {
+    return *p;
+  } else {
+    return l2::ld(p, pol);
+  }
+}
+
 // The four reads c1, c3, c4, c2 of point k2 of one item.
-template <int L, bool MAPPED>
+template <int L, bool MAPPED, bool STAGED = false>
 __device__ __forceinline__ float4 inv_reads(const InvRows& r, int k2, bool rev, bool swapc, uint64_t pol) {
   const int km = (L - k2) & (L - 1);
   float c1, c3, c4, c2;
   if constexpr (!MAPPED) {
-    c1 = r.ra ? l2::ld(r.ra + k2, pol) : 0.f;
-    c3 = l2::ld(r.rb + k2, pol);
-    c4 = (k2 && r.ra) ? l2::ld(r.ra + km, pol) : 0.f;
-    c2 = k2 ? l2::ld(r.rb + km, pol) : 0.f;
+    c1 = r.ra ? inv_ld<STAGED>(r.ra + k2, pol) : 0.f;
+    c3 = inv_ld<STAGED>(r.rb + k2, pol);
+    c4 = (k2 && r.ra) ? inv_ld<STAGED>(r.ra + km, pol) : 0.f;
+    c2 = k2 ? inv_ld<STAGED>(r.rb + km, pol) : 0.f;
   } else {
     const int ka = swapc ? km : k2, kb = swapc ? k2 : km;
     const int pa = rev ? L - 1 - ka : ka, pb = rev ? L - 1 - kb : kb;
     const bool z0 = swapc && !k2;
-    c1 = (!r.ra || z0) ? 0.f : l2::ld(r.ra + pa, pol);
-    c3 = z0 ? 0.f : l2::ld(r.rb + pa, pol);
-    c4 = (k2 && r.ra) ? l2::ld(r.ra + pb, pol) : 0.f;
-    c2 = k2 ? l2::ld(r.rb + pb, pol) : 0.f;
+    c1 = (!r.ra || z0) ? 0.f : inv_ld<STAGED>(r.ra + pa, pol);
+    c3 = z0 ? 0.f : inv_ld<STAGED>(r.rb + pa, pol);
+    c4 = (k2 && r.ra) ? inv_ld<STAGED>(r.ra + pb, pol) : 0.f;
+    c2 = k2 ? inv_ld<STAGED>(r.rb + pb, pol) : 0.f;
   }
   return make_float4(c1, c3, c4, c2);
 }
 
-template <int L, bool MAPPED, bool PACKED>
+template <int L, bool MAPPED, bool PACKED, bool STAGED = false>
 __device__ __forceinline__ void inv_pre_x2(const Dct2dArgs& a, const InvRows& A, const InvRows& B, int k1, int kb,
                                            int g, soa::C2* v) {
   constexpr int TPS = fft_tps(L);
@@ -882,8 +893,8 @@ __device__ __forceinline__ void inv_pre_x2(const Dct2dArgs& a, const InvRows& A,
   for (int jj = 0; jj < 16; ++jj) {
     const int j = (jj & 1) ? 15 - (jj >> 1) : (jj >> 1);
     const int k2 = g + TPS * j;
-    const float4 ca = inv_reads<L, MAPPED>(A, k2, rev, swapc, pol);
-    const float4 cb = inv_reads<L, MAPPED>(B, k2, rev, swapc, pol);
+    const float4 ca = inv_reads<L, MAPPED, STAGED>(A, k2, rev, swapc, pol);
+    const float4 cb = inv_reads<L, MAPPED, STAGED>(B, k2, rev, swapc, pol);
     const float2 bk = __ldg(a.ib + k2);
     // x = (c1 - c2, -(c3 + c4)), v = x b ia
     const soa::C2 x{make_float2(ca.x - ca.w, cb.x - cb.w), make_float2(-(ca.y + ca.z), -(cb.y + cb.z))};

@@ -14,19 +14,32 @@ cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_fwd<L>),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, false>),
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, false, false>),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, true>),
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, true, false>),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, false, true>),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TpRowGeom<L>::SMEM_STAGED);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, true, true>),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TpRowGeom<L>::SMEM_STAGED);
     return e;
   }
   if ((a.n1 / 4) % R::NP) return cudaErrorInvalidValue;
   const dim3 grid(a.n1 / 4 / R::NP, 1, batch);
-  if (inverse && (a.vkind == 1 || a.vkind == 2))
-    return pdl::launch(k_tp_rows_inv<L, true>, grid, dim3(R::THREADS), R::SMEM, s, a);
+  // device input: the rows are staged by bulk copies; host-mapped input: read directly
+  const size_t smem_st = TpRowGeom<L>::SMEM_STAGED;
+  const bool mapped = a.vkind == 1 || a.vkind == 2;
+  if (inverse && a.io_dev && mapped)
+    return pdl::launch(k_tp_rows_inv<L, true, true>, grid, dim3(R::THREADS), smem_st, s, a);
+  else if (inverse && a.io_dev)
+    return pdl::launch(k_tp_rows_inv<L, false, true>, grid, dim3(R::THREADS), smem_st, s, a);
+  else if (inverse && mapped)
+    return pdl::launch(k_tp_rows_inv<L, true, false>, grid, dim3(R::THREADS), R::SMEM, s, a);
   else if (inverse)
-    return pdl::launch(k_tp_rows_inv<L, false>, grid, dim3(R::THREADS), R::SMEM, s, a);
+    return pdl::launch(k_tp_rows_inv<L, false, false>, grid, dim3(R::THREADS), R::SMEM, s, a);
   else
     return pdl::launch(k_tp_rows_fwd<L>, grid, dim3(R::THREADS), R::SMEM, s, a);
 }

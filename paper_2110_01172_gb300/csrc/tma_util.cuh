@@ -91,6 +91,16 @@ __device__ __forceinline__ void load_4d(void* dst, const CUtensorMap* map, int x
       : "memory");
 }
 
+// Contiguous bulk copy global -> shared memory (16-byte aligned addresses,
+// size a multiple of 16), completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar)), "l"(pol)
+      : "memory");
+}
+
 // Tiled tensor stores from shared memory (bulk-group completion).
 __device__ __forceinline__ void store_3d(const CUtensorMap* map, const void* src, int x, int y, int z, uint64_t pol) {
   asm volatile(
