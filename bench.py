@@ -50,10 +50,10 @@ FALLBACK_HBM_GBS = 6800.0
 # launches, so the workspace stays in L2 as it does here).  Valid only for the
 # kernel sources with this digest; otherwise reported as null.
 TRAFFIC = {
-    "sources_sha256": "285eed1c4d8939c2a11aa50ec316bfc1c01c586fd90f9802ea3e8c04cb444744",
+    "sources_sha256": "df1620fb0ff80f8a3b74c20e06aae00dbfb324bdafe1819339f7f2a9a5a3f4c0",
     "family": "tp",
-    "forward_bytes": 169684480,
-    "inverse_bytes": 154333696,
+    "forward_bytes": 161694464,
+    "inverse_bytes": 153027584,
 }
 
 
