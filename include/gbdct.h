@@ -207,13 +207,14 @@ gbdct_status gbdct_plan_create_family(gbdct_plan_t* out, int ndim, const int64_t
 
 /*
  * Autotuned plan: times one forward + inverse (inverse only for the
- * inverse-only kinds) of every kernel family that supports the shape and batch,
- * on scratch buffers it allocates and frees, with CUDA events on a private
+ * inverse-only kinds) of every candidate that supports the shape and batch —
+ * the kernel families and their tile parameters ("fs2/<A>" four-step splits,
+ * "tp/<NP>" two-pass strip widths) — on scratch buffers it allocates and frees, with CUDA events on a private
  * stream, and returns the plan of the fastest.  The choice is cached for the
  * process and, when the environment variable GBDCT_TUNE_CACHE names a file,
  * appended to that file ("key family microseconds" lines) and read back by
  * later processes, which then create the plan without timing.  family_out
- * (optional, family_cap bytes) receives the chosen family's name.
+ * (optional, family_cap bytes) receives the chosen candidate's name.
  * Synchronises the device.  Errors as gbdct_plan_create_batched.
  */
 gbdct_status gbdct_plan_create_tuned(gbdct_plan_t* out, int ndim, const int64_t* dims, int64_t batch, int kind,

@@ -146,7 +146,8 @@ class Plan:
 
     def __init__(self, shape, kind: str = "dct2", batch: int = 1, device=None, family: str | None = None,
                  tuned: bool = False):
-        """family: force a kernel family ("seq", "pair", "fs2", "tp", or "fs2/<A>");
+        """family: force a kernel family ("seq", "pair", "fs2", "tp", "fs2/<A>" for a
+        four-step split, or "tp/<NP>" for a two-pass strip width);
         tuned: pick the fastest family by timing (gbdct_plan_create_tuned)."""
         torch = _torch()
         lib = load()
@@ -160,7 +161,7 @@ class Plan:
         dims = (ctypes.c_int64 * len(self.shape))(*self.shape)
         handle = ctypes.c_void_p()
         args = (ctypes.byref(handle), len(self.shape), dims, self.batch, KINDS[kind], F32)
-        self.choice = family   # the forced or tuned family / four-step split, e.g. "fs2/32"
+        self.choice = family   # the forced or tuned family / tile choice, e.g. "fs2/32", "tp/2"
         with torch.cuda.device(self.device):
             if family is not None:
                 _check(lib.gbdct_plan_create_family(*args, family.encode()), "gbdct_plan_create_family")
