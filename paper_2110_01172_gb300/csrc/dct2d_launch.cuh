@@ -65,12 +65,12 @@ cudaError_t run_tp(int log2N1, int log2N2, bool inverse, const Dct2dArgs& a, int
 cudaError_t run_tp_cols(int lg1, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare);
 constexpr int kTpMinLog2N1 = 7, kTpMaxLog2N1 = 13, kTpMinLog2N2 = 7, kTpMaxLog2N2 = 13;
 // Strip widths NP (column pairs per CTA) the two-pass column pass is built
-// for at half-length M: 128 to 512 threads (M/16 per pair), the strip's
+// for at half-length M: 64 to 512 threads (M/16 per pair), the strip's
 // padded shared memory within 227 KB, and N2/4 float4 columns a multiple of NP.
 inline bool tp_strip_ok(int M, int n2, int np) {
   const int threads = np * (M / 16);
   const size_t smem = (size_t)np * (M + M / 16) * 16;
-  return np >= 1 && threads >= 128 && threads <= 512 && smem <= 227 * 1024 - 256 && (n2 / 4) % np == 0;
+  return np >= 1 && threads >= 64 && threads <= 512 && smem <= 227 * 1024 - 256 && (n2 / 4) % np == 0;
 }
 
 constexpr int kPairMinLog2 = 4;

@@ -40,7 +40,7 @@ namespace gbdct {
 // of a CTA are interleaved point by point in shared memory and thread
 // t = g * NP + pi is rank g of pair pi, so a warp's loads and stores cover
 // 32/NP rows x NP*16 contiguous bytes.  NP (the strip width, a tile
-// parameter the autotuner can choose) keeps the CTA at 128 to 512 threads
+// parameter the autotuner can choose) keeps the CTA at 64 to 512 threads
 // and its shared memory within one SM.
 // ----------------------------------------------------------------------------
 template <int M, int NP_>
@@ -54,7 +54,7 @@ struct TpColGeom {
   // faster than two at 128 registers (4096^2: 35.5 / 33.3 us vs 37.6 / 37.4),
   // the CTAs' strip loads overlapping the others' FFTs; else 128 registers
   static constexpr int MINB = THREADS == 256 ? 3 : (THREADS <= 512 ? 512 / THREADS : 1);
-  static constexpr bool VALID = THREADS >= 128 && THREADS <= 512 && SMEM <= 227 * 1024 - 256;
+  static constexpr bool VALID = THREADS >= 64 && THREADS <= 512 && SMEM <= 227 * 1024 - 256;
   // bulk tensor copy form: + 128-byte alignment slack, the mbarrier and a flag
   static constexpr size_t SMEM_TMA = SMEM + 256;
   static constexpr int HALF = M / 2;                    // rows of one reorder residue
@@ -249,19 +249,28 @@ __global__ void __launch_bounds__(TpColGeom<M, NP>::THREADS, TpColGeom<M, NP>::M
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ int tp_item_b(int c, int M) { return c ? M - c : M / 2; }
 
-// Shared memory of the inverse row pass with staged rows: the groups' buffers
-// + one 8-byte barrier per group and the CTA's 4-byte flag (16 bytes of slack).
-// (Staging the forward row pass's workspace rows the same way measured slower,
-// 36.2 vs 33.5 us at 4096^2: its loads already hit L2 and are read once.)
-template <int L>
-struct TpRowGeom {
-  using R = RowX2Geom<L>;
-  static constexpr size_t SMEM_STAGED = R::SMEM + (size_t)R::NP * 8 + 16;
+// Row-pass geometry: NP item pairs per CTA, TPS = L/16 threads each.  Wide
+// CTAs have 256 threads (the four-step family's row geometry); narrow ones 64,
+// for grids that would otherwise leave SMs idle (a single transform with few
+// rows: 1024^2 has 256 item pairs, 64 wide CTAs for 152 SMs).  SMEM_STAGED
+// adds one 8-byte barrier per group and the CTA's 4-byte flag (16 bytes of
+// slack) for the inverse pass's staged rows.  (Staging the forward row pass's
+// workspace rows the same way measured slower, 36.2 vs 33.5 us at 4096^2: its
+// loads already hit L2 and are read once.)
+template <int L, bool NARROW>
+struct TpRows {
+  static constexpr int TPS = fft_tps(L);
+  static constexpr int NP = ((NARROW ? 64 : 256) / TPS) > 0 ? (NARROW ? 64 : 256) / TPS : 1;
+  static constexpr int THREADS = NP * TPS;
+  static constexpr int LP = L + L / 16;
+  static constexpr size_t SMEM = (size_t)NP * LP * sizeof(float4);
+  static constexpr size_t SMEM_STAGED = SMEM + (size_t)NP * 8 + 16;
+  static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;  // up to 128 registers
 };
 
-template <int L>
-__global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB) k_tp_rows_fwd(Dct2dArgs a) {
-  using R = RowX2Geom<L>;
+template <int L, bool NARROW>
+__global__ void __launch_bounds__(TpRows<L, NARROW>::THREADS, TpRows<L, NARROW>::MINB) k_tp_rows_fwd(Dct2dArgs a) {
+  using R = TpRows<L, NARROW>;
   constexpr int TPS = R::TPS;
   constexpr int MASK = mirror_lane_mask<TPS>();
   extern __shared__ float4 sxt[];
@@ -347,9 +356,9 @@ __device__ __forceinline__ void tp_inv_pair(const float4* __restrict__ s, const 
 // buffer (17 L bytes) holds the 16 L bytes of the rows until the first FFT
 // stage overwrites it.  Device buffers only.
 
-template <int L, bool MAPPED, bool STAGED>
-__global__ void __launch_bounds__(RowX2Geom<L>::THREADS, RowX2Geom<L>::MINB_INV) k_tp_rows_inv(Dct2dArgs a) {
-  using R = RowX2Geom<L>;
+template <int L, bool MAPPED, bool STAGED, bool NARROW>
+__global__ void __launch_bounds__(TpRows<L, NARROW>::THREADS, TpRows<L, NARROW>::MINB) k_tp_rows_inv(Dct2dArgs a) {
+  using R = TpRows<L, NARROW>;
   extern __shared__ float4 sxti[];
   const int pi = threadIdx.x / R::TPS, g = threadIdx.x % R::TPS;
   float4* s = sxti + pi * R::LP;

@@ -428,8 +428,9 @@ static gbdct_status create_impl(gbdct_plan_t* out, int ndim, const int64_t* dims
   // group (fastest measured at every shape they share: e.g. 128^2 11.9 vs
   // 15.8 us (pair), 256^2 11.8 vs 16.5 (fs2), 4096^2 69.5 vs 76.3; at
   // N1 = 8192 the four-step column steps beat the two-pass column pass, whose
-  // strips there are 32 bytes of 4096 rows).
-  p->family = (tp && p->lg1 <= 12) ? FAM_TP : fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
+  // strips there are 32 bytes of 4096 rows, where they apply: 8192 x 128 runs
+  // two-pass, 18 / 20 us vs 27 / 30 us with pair).
+  p->family = (tp && (p->lg1 <= 12 || !fs2)) ? FAM_TP : fs2 ? FAM_FS2 : (pair ? FAM_PAIR : FAM_SEQ);
   // GBDCT_KERNEL_FAMILY=seq|pair|fs2 forces a family when it supports the shape
   // (used to test and compare every kernel family on the same inputs).
   if (const char* f = fname) {

@@ -67,9 +67,37 @@ cudaError_t col_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t
   }
 }
 
+// The strip width: the plan's choice, else the default for M, halved (down
+// to two column pairs and 64 threads) while the grid would give fewer than
+// two CTAs per SM (a single transform with few columns, e.g. 1024^2).
+template <int M>
+int strip_np(const Dct2dArgs& a, int batch) {
+  if (a.tpNP) return a.tpNP;
+  int np = tp_default_np(M);
+  const long long nsm = a.nsm > 0 ? a.nsm : 1;
+  while (np > 2 && (np / 2) * fft_tps(M) >= 64 && (long long)(a.n2 / 4 / np) * 2 * batch < 2 * nsm) np /= 2;
+  return np;
+}
+
 template <int M>
 cudaError_t col_np(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
-  switch (a.tpNP ? a.tpNP : tp_default_np(M)) {  // strip width in column pairs
+  if (prepare) {  // every width the default or the grid rule can pick
+    cudaError_t e = cudaSuccess;
+    for (int np = (a.tpNP ? a.tpNP : tp_default_np(M)); np >= 1 && e == cudaSuccess; np /= 2) {
+      switch (np) {
+        case 1: e = col_launch<M, 1>(inverse, a, batch, s, true); break;
+        case 2: e = col_launch<M, 2>(inverse, a, batch, s, true); break;
+        case 4: e = col_launch<M, 4>(inverse, a, batch, s, true); break;
+        case 8: e = col_launch<M, 8>(inverse, a, batch, s, true); break;
+        case 16: e = col_launch<M, 16>(inverse, a, batch, s, true); break;
+        case 32: e = col_launch<M, 32>(inverse, a, batch, s, true); break;
+      }
+      if (e == cudaErrorInvalidValue) e = cudaSuccess;  // width not built for this M
+      if (a.tpNP) break;
+    }
+    return e;
+  }
+  switch (strip_np<M>(a, batch)) {  // strip width in column pairs
     case 1: return col_launch<M, 1>(inverse, a, batch, s, prepare);
     case 2: return col_launch<M, 2>(inverse, a, batch, s, prepare);
     case 4: return col_launch<M, 4>(inverse, a, batch, s, prepare);

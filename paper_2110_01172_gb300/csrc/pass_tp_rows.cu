@@ -7,41 +7,51 @@
 namespace gbdct {
 namespace {
 
-template <int L>
-cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
-  using R = RowX2Geom<L>;
+template <int L, bool NARROW>
+cudaError_t row_launch_g(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  using R = TpRows<L, NARROW>;
   if (prepare) {
-    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_fwd<L>),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, false, false>),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, true, false>),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, false, true>),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TpRowGeom<L>::SMEM_STAGED);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_tp_rows_inv<L, true, true>),
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TpRowGeom<L>::SMEM_STAGED);
+    const void* plain[] = {reinterpret_cast<const void*>(k_tp_rows_fwd<L, NARROW>),
+                           reinterpret_cast<const void*>(k_tp_rows_inv<L, false, false, NARROW>),
+                           reinterpret_cast<const void*>(k_tp_rows_inv<L, true, false, NARROW>)};
+    const void* staged[] = {reinterpret_cast<const void*>(k_tp_rows_inv<L, false, true, NARROW>),
+                            reinterpret_cast<const void*>(k_tp_rows_inv<L, true, true, NARROW>)};
+    cudaError_t e = cudaSuccess;
+    for (const void* k : plain)
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    for (const void* k : staged)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM_STAGED);
     return e;
   }
   if ((a.n1 / 4) % R::NP) return cudaErrorInvalidValue;
   const dim3 grid(a.n1 / 4 / R::NP, 1, batch);
-  // device input: the rows are staged by bulk copies; host-mapped input: read directly
-  const size_t smem_st = TpRowGeom<L>::SMEM_STAGED;
+  // device input: the inverse's rows are staged by bulk copies; host-mapped input: read directly
   const bool mapped = a.vkind == 1 || a.vkind == 2;
   if (inverse && a.io_dev && mapped)
-    return pdl::launch(k_tp_rows_inv<L, true, true>, grid, dim3(R::THREADS), smem_st, s, a);
+    return pdl::launch(k_tp_rows_inv<L, true, true, NARROW>, grid, dim3(R::THREADS), R::SMEM_STAGED, s, a);
   else if (inverse && a.io_dev)
-    return pdl::launch(k_tp_rows_inv<L, false, true>, grid, dim3(R::THREADS), smem_st, s, a);
+    return pdl::launch(k_tp_rows_inv<L, false, true, NARROW>, grid, dim3(R::THREADS), R::SMEM_STAGED, s, a);
   else if (inverse && mapped)
-    return pdl::launch(k_tp_rows_inv<L, true, false>, grid, dim3(R::THREADS), R::SMEM, s, a);
+    return pdl::launch(k_tp_rows_inv<L, true, false, NARROW>, grid, dim3(R::THREADS), R::SMEM, s, a);
   else if (inverse)
-    return pdl::launch(k_tp_rows_inv<L, false, false>, grid, dim3(R::THREADS), R::SMEM, s, a);
+    return pdl::launch(k_tp_rows_inv<L, false, false, NARROW>, grid, dim3(R::THREADS), R::SMEM, s, a);
   else
-    return pdl::launch(k_tp_rows_fwd<L>, grid, dim3(R::THREADS), R::SMEM, s, a);
+    return pdl::launch(k_tp_rows_fwd<L, NARROW>, grid, dim3(R::THREADS), R::SMEM, s, a);
+}
+
+// Narrow (64-thread) CTAs when wide ones would give fewer than two CTAs per SM.
+template <int L>
+cudaError_t row_launch(bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {
+  if (prepare) {
+    cudaError_t e = row_launch_g<L, false>(inverse, a, batch, s, true);
+    if (e == cudaSuccess) e = row_launch_g<L, true>(inverse, a, batch, s, true);
+    return e;
+  }
+  const long long wide_ctas = (long long)(a.n1 / 4 / TpRows<L, false>::NP) * batch;
+  if (wide_ctas < 2LL * (a.nsm > 0 ? a.nsm : 1) && (a.n1 / 4) % TpRows<L, true>::NP == 0)
+    return row_launch_g<L, true>(inverse, a, batch, s, false);
+  return row_launch_g<L, false>(inverse, a, batch, s, false);
 }
 
 cudaError_t run_rows(int lg2, bool inverse, const Dct2dArgs& a, int batch, cudaStream_t s, bool prepare) {

@@ -108,7 +108,7 @@ def strip_ok(m, n2, np_):
     """Strip widths the column pass is built for (tp_strip_ok in dct2d_launch.cuh)."""
     threads = np_ * (m // 16)
     smem = np_ * (m + m // 16) * 16
-    return 128 <= threads <= 512 and smem <= 227 * 1024 - 256 and (n2 // 4) % np_ == 0
+    return 64 <= threads <= 512 and smem <= 227 * 1024 - 256 and (n2 // 4) % np_ == 0
 
 
 @pytest.mark.parametrize("n1", SIZES)
