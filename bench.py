@@ -50,10 +50,10 @@ FALLBACK_HBM_GBS = 6800.0
 # launches, so the workspace stays in L2 as it does here).  Valid only for the
 # kernel sources with this digest; otherwise reported as null.
 TRAFFIC = {
-    "sources_sha256": "df1620fb0ff80f8a3b74c20e06aae00dbfb324bdafe1819339f7f2a9a5a3f4c0",
+    "sources_sha256": "c65eb368e1eeb8a80a7c5d1a9a03d361187dc9ab315b758b1b4701972b81dc6d",
     "family": "tp",
-    "forward_bytes": 161694464,
-    "inverse_bytes": 153027584,
+    "forward_bytes": 162805504,
+    "inverse_bytes": 153853184,
 }
 
 
