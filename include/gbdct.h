@@ -121,7 +121,10 @@ gbdct_status gbdct_plan_create_batched(gbdct_plan_t* out, int ndim, const int64_
  * memory of the plan's device, managed memory, or page-locked host memory
  * (cudaHostAlloc / cudaHostRegister, mapped at the same address): host
  * buffers are read and written by the transform's own first and last kernels
- * over the host link, with no staging copy.  Pageable host memory is accepted
+ * over the host link, with no staging copy (a two-pass plan runs such calls
+ * with its four-step launches, which access whole row segments, where that
+ * family supports the shape; results then differ from the device-buffer call
+ * in FP32 rounding only).  Pageable host memory is accepted
  * only where the device can access it (cudaDevAttrPageableMemoryAccess).  The
  * call is asynchronous on `stream`; the caller keeps both buffers alive until
  * the stream has passed the work.  Errors: INVALID_ARG (NULL, misaligned or
