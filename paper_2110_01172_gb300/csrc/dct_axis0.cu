@@ -3,6 +3,8 @@
 
 #include "dct2d_kernels.cuh"
 #include "fft_core.cuh"
+#include "fft_soa.cuh"
+#include "l2_hint.cuh"
 #include "launch_dep.cuh"
 
 namespace gbdct {
@@ -91,8 +93,111 @@ __global__ void __launch_bounds__(512, 2) k_axis0(AxisArgs a) {
   }
 }
 
+// Packed form, N >= 64: NP two-lane sequences (float4 = two adjacent column
+// pairs of a row) per CTA, TPS = N/16 threads each, 128 threads per CTA.
+template <int N>
+struct AxisSoaGeom {
+  static constexpr int TPS = fft_tps(N);
+  static constexpr int NP = (128 / TPS) > 0 ? 128 / TPS : 1;
+  static constexpr int THREADS = NP * TPS;
+  static constexpr int LP = N + N / 16;
+  static constexpr size_t SMEM = (size_t)NP * LP * sizeof(float4);
+  static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;  // up to 128 registers
+};
+
+template <int N, bool INV>
+__global__ void __launch_bounds__(AxisSoaGeom<N>::THREADS, AxisSoaGeom<N>::MINB) k_axis0_soa(AxisArgs a) {
+  using G = AxisSoaGeom<N>;
+  constexpr int TPS = G::TPS, NP = G::NP;
+  extern __shared__ float4 sas[];
+  const int pi = threadIdx.x % NP, g = threadIdx.x / NP;
+  const long long hv = a.M / 4;  // float4 per row
+  const long long vcol = (long long)blockIdx.x * NP + pi;
+  const float4* X = reinterpret_cast<const float4*>(a.in + (long long)blockIdx.y * a.bstride) + vcol;
+  float4* Y = reinterpret_cast<float4*>(a.out + (long long)blockIdx.y * a.bstride) + vcol;
+  float4* s = sas + pi;
+  const uint64_t pol = l2::evict_first();
+  soa::C2 v[16];
+  pdl::wait_prior_grid();
+  if constexpr (!INV) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = soa::unpack_aos(l2::ld_once(X + reorder_src(g + TPS * j, N) * hv, pol));
+    soa::first_stage<N, false, NP>(v, s, g);
+    __syncthreads();
+    soa::stages<N, 16, false, NP>(s, g, a.tw4);
+    pdl::launch_dependents();
+#pragma unroll 4
+    for (int r = 0; r < 16; ++r) {
+      const int k = g + TPS * r;
+      const soa::C2 zk = soa::unpack(s[NP * soa::pidx4(k)]);
+      const soa::C2 zm = soa::unpack(s[NP * soa::pidx4((N - k) & (N - 1))]);
+      const float2 w = __ldg(a.w + k);  // e^{-i pi k / 2N} / 2
+      // per lane: 2 Va = Z[k] + conj Z[N-k], 2 Vb = -i (Z[k] - conj Z[N-k]); X = Re(w 2V)
+      const float2 va_r = soa::add2(zk.re, zm.re), va_i = soa::sub2(zk.im, zm.im);
+      const float2 vb_r = soa::add2(zk.im, zm.im), vb_i = soa::sub2(zm.re, zk.re);
+      const float2 xa = soa::fma2(va_i, soa::bc(-w.y), soa::mul2(va_r, soa::bc(w.x)));
+      const float2 xb = soa::fma2(vb_i, soa::bc(-w.y), soa::mul2(vb_r, soa::bc(w.x)));
+      l2::st(Y + (long long)k * hv, make_float4(xa.x, xb.x, xa.y, xb.y), pol);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      v[j] = soa::unpack_aos(l2::ld_once(X + (long long)(g + TPS * j) * hv, pol));
+      s[NP * soa::pidx4(g + TPS * j)] = soa::pack(v[j]);
+    }
+    __syncthreads();
+    // Z[k] = Va[k] + i Vb[k] from rows k and N-k (row N taken as zero)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = g + TPS * j;
+      const soa::C2 c = v[j];
+      const soa::C2 m = k ? soa::unpack(s[NP * soa::pidx4(N - k)]) : soa::C2{soa::bc(0.f), soa::bc(0.f)};
+      const float2 w = __ldg(a.w + k);  // e^{+i pi k / 2N} / N
+      // per lane: Va = w (X_a[k] - i X_a[N-k]), Vb = w (X_b[k] - i X_b[N-k]);
+      // lane values: X_a = re, X_b = im of the packed column pair
+      const soa::C2 va = soa::mulw(soa::C2{c.re, soa::ng(m.re)}, soa::bc(w.x), soa::bc(w.y));
+      const soa::C2 vb = soa::mulw(soa::C2{c.im, soa::ng(m.im)}, soa::bc(w.x), soa::bc(w.y));
+      v[j] = soa::C2{soa::sub2(va.re, vb.im), soa::add2(va.im, vb.re)};
+    }
+    __syncthreads();  // the first stage overwrites the staged rows
+    soa::first_stage<N, true, NP>(v, s, g);
+    __syncthreads();
+    soa::stages<N, 16, true, NP>(s, g, a.tw4);
+    pdl::launch_dependents();
+#pragma unroll 4
+    for (int r = 0; r < 16; ++r) {
+      const int n = g + TPS * r;
+      l2::st(Y + (long long)reorder_src(n, N) * hv, soa::pack_aos(soa::unpack(s[NP * soa::pidx4(n)])), pol);
+    }
+  }
+}
+
+template <int N>
+cudaError_t launch_soa(bool inverse, const AxisArgs& a, int batch, cudaStream_t s, bool prepare) {
+  using G = AxisSoaGeom<N>;
+  if (prepare) {
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_axis0_soa<N, false>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_axis0_soa<N, true>),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    return e;
+  }
+  const long long ctas = a.M / 4 / G::NP;
+  if (a.M % (4LL * G::NP) || ctas < 1 || ctas > 0x7fffffffLL || batch < 1 || batch > 65535)
+    return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)ctas, (unsigned)batch);
+  if (inverse) return pdl::launch(k_axis0_soa<N, true>, grid, dim3(G::THREADS), G::SMEM, s, a);
+  return pdl::launch(k_axis0_soa<N, false>, grid, dim3(G::THREADS), G::SMEM, s, a);
+}
+
 template <int N>
 cudaError_t launch(bool inverse, const AxisArgs& a, int batch, cudaStream_t s, bool prepare) {
+  if constexpr (N >= 64) {
+    // the packed form where the strip width divides the columns (always for
+    // power-of-two slices of at least 4 x 32 elements)
+    if (a.tw4 && a.M % (4LL * AxisSoaGeom<N>::NP) == 0) return launch_soa<N>(inverse, a, batch, s, prepare);
+  }
   using G = AxisGeom<N>;
   const int P = 1 << a.lgP;
   const size_t smem = (size_t)P * G::SP * sizeof(float2);

@@ -13,10 +13,14 @@
 //            X_a[k] = Re(e^{-i pi k / 2N} Va[k]),  X_b likewise
 //   inverse  Va[k] = e^{+i pi k / 2N} (X_a[k] - i X_a[N-k]) / N   (X_a[N] = 0)
 //            z = IFFT_N(Va + i Vb);  x[s(n), 2p] = Re z[n], x[s(n), 2p+1] = Im z[n]
-// One CTA holds all N rows of P column pairs in shared memory (sequence
-// stride odd, so that a warp reading one row across sequences is conflict-free),
-// runs the P length-N FFTs with the Stockham engine of fft_core.cuh, and writes
-// the same tile back (so the pass may run in place).
+// One CTA holds all N rows of a strip of columns in shared memory and writes
+// the same strip back (so the pass may run in place).  For N >= 64 (the
+// packed form) a float4 of a row, two adjacent column pairs, is one two-lane
+// sequence of the packed-FP32x2 Stockham engine (fft_soa.cuh), NP such
+// sequences per CTA interleaved point by point so that a warp's loads and
+// stores cover 32/NP rows x NP*16 contiguous bytes; below 64 one CTA holds P
+// column pairs as one complex sequence each (fft_core.cuh, sequence stride
+// odd so that a warp reading one row across sequences is conflict-free).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -29,6 +33,7 @@ struct AxisArgs {
   long long M;          // real columns (contiguous extent)
   long long bstride;    // floats between batch items
   const float2* tw;     // stage twiddles of the length-N FFT (pmax 16)
+  const float4* tw4;    // the same as (wr, wr, wi, wi), for the packed two-lane form
   const float2* w;      // forward: e^{-i pi k / 2N} / 2; inverse: e^{+i pi k / 2N} / N  (k < N)
   int lgP;              // log2 of the column pairs per CTA
 };

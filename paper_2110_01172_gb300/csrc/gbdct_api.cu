@@ -281,11 +281,17 @@ static gbdct_status create_3d(gbdct_plan_t* out, const int64_t* dims, int64_t ba
   const int n0 = (int)dims[0];
   const int tot = gbdct::tw_size_p(n0, 16);
   const size_t t0 = round_up(tot + 1, 2), tn = round_up(n0, 2);
-  cudaError_t e = cudaMalloc(&p->ax_tables, (t0 + 2 * tn) * sizeof(float2));
+  // stage twiddles (float2, then the same as float4 for the packed form), forward post, inverse pre
+  cudaError_t e = cudaMalloc(&p->ax_tables, (3 * t0 + 2 * tn) * sizeof(float2));
+  float4* tw4 = nullptr;
   if (e == cudaSuccess) {
     float2* fw = p->ax_tables + t0;
     float2* iw = fw + tn;
-    if (tot > 0) k_gen_stage_twiddles<<<(tot + 255) / 256, 256>>>(p->ax_tables, n0, 16, tot);
+    tw4 = reinterpret_cast<float4*>(iw + tn);
+    if (tot > 0) {
+      k_gen_stage_twiddles<<<(tot + 255) / 256, 256>>>(p->ax_tables, n0, 16, tot);
+      k_expand_twiddles<<<(tot + 255) / 256, 256>>>(p->ax_tables, tw4, tot);
+    }
     k_gen_axis_tables<<<(n0 + 255) / 256, 256>>>(fw, iw, n0);
     p->ax_fw = fw;
     p->ax_iw = iw;
@@ -295,6 +301,7 @@ static gbdct_status create_3d(gbdct_plan_t* out, const int64_t* dims, int64_t ba
   p->ax.M = dims[1] * dims[2];
   p->ax.bstride = dims[0] * dims[1] * dims[2];
   p->ax.tw = p->ax_tables;
+  p->ax.tw4 = tw4;
   p->ax.lgP = gbdct::axis0_lgP(lg0, p->ax.M);
   if (e == cudaSuccess) e = gbdct::run_axis0(lg0, false, p->ax, 1, 0, true);
   if (e != cudaSuccess) {
