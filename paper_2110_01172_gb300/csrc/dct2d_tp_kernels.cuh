@@ -65,8 +65,8 @@ struct TpColGeom {
 // 256 threads, 74 / 76 us vs 87 / 87 us at 512 threads).
 __host__ __device__ constexpr int tp_default_np(int M) { return 128 / fft_tps(M) > 2 ? 128 / fft_tps(M) : 2; }
 
-__device__ __forceinline__ soa::C2 aos_to_soa(float4 q) { return soa::unpack_aos(q); }
-__device__ __forceinline__ float4 soa_to_aos(soa::C2 y) { return soa::pack_aos(y); }
+__device__ __forceinline__ soa::C2 aos_to_soa(float4 q) { return {make_float2(q.x, q.z), make_float2(q.y, q.w)}; }
+__device__ __forceinline__ float4 soa_to_aos(soa::C2 y) { return make_float4(y.re.x, y.im.x, y.re.y, y.im.y); }
 
 // Forward (INV = false): reorder + E or O (blockIdx.y = parity of the
 // reordered row) -> workspace.  Inverse: E' or O' -> IDFT_M -> output rows

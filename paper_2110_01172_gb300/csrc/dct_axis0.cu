@@ -93,6 +93,10 @@ __global__ void __launch_bounds__(512, 2) k_axis0(AxisArgs a) {
   }
 }
 
+// A float4 of a row (two adjacent column pairs (re_a, im_a, re_b, im_b)) as
+// one point of a two-lane sequence.
+__device__ __forceinline__ soa::C2 pairs_to_soa(float4 q) { return {make_float2(q.x, q.z), make_float2(q.y, q.w)}; }
+
 // Packed form, N >= 64: NP two-lane sequences (float4 = two adjacent column
 // pairs of a row) per CTA, TPS = N/16 threads each, 128 threads per CTA.
 template <int N>
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(AxisSoaGeom<N>::THREADS, AxisSoaGeom<N>::MINB)
   pdl::wait_prior_grid();
   if constexpr (!INV) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = soa::unpack_aos(l2::ld_once(X + reorder_src(g + TPS * j, N) * hv, pol));
+    for (int j = 0; j < 16; ++j) v[j] = pairs_to_soa(l2::ld_once(X + reorder_src(g + TPS * j, N) * hv, pol));
     soa::first_stage<N, false, NP>(v, s, g);
     __syncthreads();
     soa::stages<N, 16, false, NP>(s, g, a.tw4);
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(AxisSoaGeom<N>::THREADS, AxisSoaGeom<N>::MINB)
   } else {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      v[j] = soa::unpack_aos(l2::ld_once(X + (long long)(g + TPS * j) * hv, pol));
+      v[j] = pairs_to_soa(l2::ld_once(X + (long long)(g + TPS * j) * hv, pol));
       s[NP * soa::pidx4(g + TPS * j)] = soa::pack(v[j]);
     }
     __syncthreads();

@@ -54,7 +54,6 @@ __device__ __forceinline__ float4 pack(C2 a) { return make_float4(a.re.x, a.re.y
 // The two points as two interleaved complex values (re_a, im_a, re_b, im_b),
 // the layout of a pair of adjacent complex columns in global memory.
 __device__ __forceinline__ float4 pack_aos(C2 a) { return make_float4(a.re.x, a.im.x, a.re.y, a.im.y); }
-__device__ __forceinline__ C2 unpack_aos(float4 q) { return {make_float2(q.x, q.z), make_float2(q.y, q.w)}; }
 __device__ __forceinline__ C2 unpack(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
 
 // Multiply by W16^E = exp(-+2 pi i E / 16) for a compile-time E.
